@@ -1,0 +1,129 @@
+"""Pins of the CPU oracle (no GPU).  See oracle_pins.py for what each fixes."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle_pins as P
+from paper_2301_03814_gb300 import workloads as w
+from oracle.swkb_oracle import (CausticError, Medium, Oracle, RangeError, TurningError,
+                                absorber, geometry, hermite5)
+
+
+def test_hermite5_reproduces_quintics():
+    rng = np.random.default_rng(3)
+    coef = rng.standard_normal(6)
+    p = np.polynomial.Polynomial(coef)
+    z0, h, n = -1.3, 0.37, 12
+    zn = z0 + h * np.arange(n)
+    prof = w.Profile(np.array([0.0]), z0, h, p(zn)[None], p.deriv(1)(zn)[None], p.deriv(2)(zn)[None])
+    m = Medium(prof, False, 0.0)
+    z = rng.uniform(zn[0], zn[-1], 200)
+    e, ez, ezz = m.eval(0.0, True, z)
+    assert np.max(np.abs(e - p(z))) < 1e-12 * np.max(np.abs(p(z)))
+    assert np.max(np.abs(ez - p.deriv(1)(z))) < 1e-11 * np.max(np.abs(p.deriv(1)(z)))
+    assert np.max(np.abs(ezz - p.deriv(2)(z))) < 1e-10 * np.max(np.abs(p.deriv(2)(z)))
+
+
+def test_hermite5_basis_interpolates_data():
+    # t = 0 and t = 1 give back the nodal value / derivatives
+    for t, want in ((0.0, (1.0, 2.0, 3.0)), (1.0, (4.0, 5.0, 6.0))):
+        v = hermite5(1.0, 2.0, 3.0, 4.0, 5.0, 6.0, t, 0.5)
+        assert np.allclose(v, want, atol=1e-13)
+
+
+def test_mirrored_medium_is_reflection():
+    pb = w.config_surface_duct_small()
+    m = Medium(pb.profile, True, 0.0)
+    z = np.linspace(0.3, 40.0, 77)
+    a = m.eval(0.0, True, z)
+    b = m.eval(0.0, True, -z)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], -b[1]) and np.array_equal(a[2], b[2])
+
+
+def test_column_weights_left_right_limits():
+    pb = w.config_unit_periodic()
+    m = Medium(pb.profile, False, 0.0)
+    assert m.column_weights(100.0, True) == (2, 0.0)     # right limit: linear half
+    assert m.column_weights(100.0, False) == (0, 1.0)    # left limit: homogeneous half
+    c, th = m.column_weights(150.0, True)
+    assert c == 2 and abs(th - 0.5) < 1e-15
+    assert m.column_weights(-5.0, True) == (0, 0.0)
+    assert m.column_weights(500.0, False) == (2, 1.0)
+
+
+def test_geometry_counts():
+    g = geometry(w.config_unit_periodic())
+    assert (g.N, g.n_max, g.M, g.G, g.NRT) == (512, 32, 65, 96, 704)
+    g = geometry(w.config_surface_duct())
+    assert (g.N, g.n_max, g.M, g.R, g.N_r, g.G, g.NRT) == (32768, 488, 977, 16, 2048, 19, 2086)
+
+
+def test_absorber_values():
+    pb = w.config_surface_duct_small()
+    g = geometry(pb)
+    W = absorber(pb, g)
+    H = pb.z_b - pb.z_a
+    z = g.z_lo + g.dz * np.arange(g.N)
+    assert np.all(W[np.abs(z) <= 0.8 * H] == 1.0)
+    i = int(np.argmin(np.abs(np.abs(z) - 0.9 * H)))
+    assert abs(W[i] - math.cos(math.pi / 4) ** 2) < 1e-2
+    assert W[0] < 1e-12 and np.allclose(W, W[(g.N - np.arange(g.N)) % g.N])
+
+
+def test_modes_bruteforce():
+    assert P.pin_modes_bruteforce(Oracle) < 1e-13
+
+
+@pytest.mark.parametrize("bc,eps0,R,nt", [(w.BC_PERIODIC, 1.0, 1, 4), (w.BC_PERIODIC, 1.2, 4, 2),
+                                         (w.BC_NEUMANN, 1.0, 2, 4), (w.BC_DIRICHLET, 1.05, 1, 3)])
+def test_homogeneous_equals_angular_spectrum(bc, eps0, R, nt):
+    assert P.pin_homogeneous(Oracle, bc=bc, eps0=eps0, R=R, nt=nt) < 1e-12
+
+
+def test_linear_ray_closed_form_rk4_order():
+    e8 = P.pin_linear_ray(Oracle, 8)
+    e16 = P.pin_linear_ray(Oracle, 16)
+    e64 = P.pin_linear_ray(Oracle, 64)
+    assert e64 < 1e-9
+    assert 8.0 < e8 / e16 < 24.0        # fourth order
+
+
+@pytest.mark.parametrize("xdep", [False, True])
+def test_ray_tube_flux_and_jacobian(xdep):
+    assert P.pin_tube_flux(Oracle, x_dependent=xdep) < 1e-6
+
+
+def test_interpolation_stencil_remainder():
+    assert P.pin_interp_stencil(Oracle) < 1e-9
+
+
+@pytest.mark.slow
+def test_airy_exact_linear_medium():
+    assert P.pin_airy(Oracle) < 1e-4
+
+
+def test_caustic_is_an_error():
+    pb = w.config_gaussian_medium(a=0.05, b=0.01, dx=100.0, n_screens=1)
+    with pytest.raises(CausticError):
+        Oracle(pb).propagate(pb.u0)
+
+
+def test_turning_point_is_an_error():
+    k = 2 * math.pi
+    prof = w._table([0.0, 20.0], -200.0, 0.125, 3201, [w.f_const(1.0), w.f_const(0.5)])
+    z = 64.0 / 256 * np.arange(256)
+    pb = w.Problem("turn", k, 0.0, 64.0, 256, w.BC_PERIODIC, 0.0, 20.0, 1, prof,
+                   w.gaussian_beam(z, k, 32, 3, 0.0), math.radians(60.0), 1, 8)
+    with pytest.raises(TurningError):
+        Oracle(pb).propagate(pb.u0)
+
+
+def test_table_range_is_an_error():
+    k = 2 * math.pi
+    prof = w._table([0.0], -2.0, 0.125, 540, [w.f_const(1.0)])
+    z = 64.0 / 256 * np.arange(256)
+    pb = w.Problem("short", k, 0.0, 64.0, 256, w.BC_PERIODIC, 0.0, 20.0, 1, prof,
+                   w.gaussian_beam(z, k, 32, 3, 0.0), math.radians(30.0), 1, 8)
+    with pytest.raises(RangeError):
+        Oracle(pb).propagate(pb.u0)
