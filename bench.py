@@ -1,0 +1,355 @@
+#!/usr/bin/env python3
+"""Benchmark of the screened-WKB propagator on one GB300 (or N replicas).
+
+Workload (one "step" = one whole propagation, all four per-screen steps of
+Algorithm 1 for every screen): the surface duct over a reflecting ground,
+lambda = 5 cm, height 200 m, N_z = 16384 (FFT length 32768 on the mirrored
+period), 977 plane-wave modes, 10 km in 200 screens of 50 m, 16 RK4 steps and
+one ray every 16 grid points (2086 rays per mode with ghosts), seeded
+trilinear M(z) profile, 1 deg Gaussian antenna at 10 m.
+
+Metric: screen-points/s = N_z * screens / time, for the mixed FP32/FP64 path
+(value) and the FP64 path (fp64 key), with the mixed-vs-FP64 relative L2
+error of the final field.  Inputs are resident in HBM when the timed region
+starts; L2 is flushed (256 MiB write) between timed steps, outside the timed
+events.  e2e times the same propagation through the C ABI with host buffers
+(pinned), copies included.
+
+--impl reference times the FP64 CPU oracle (the only other implementation of
+the method) on a bounded sample of the same workload: one screen with every
+8th plane-wave mode, scaled by the mode count (its cost is linear in the
+number of modes).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "screen-points/s (N_z*screens/s), mixed FP32/FP64 path"
+UNIT = "screen-points/s"
+ORACLE_MODE_STRIDE = 8
+SMI_FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+FP32_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz (max SM clock)"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawTextHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload():
+    from paper_2301_03814_gb300 import workloads as w
+    return w.config_surface_duct()
+
+
+def config_dict(pb, extra=None):
+    d = {"workload": pb.name, "lambda_m": 0.05, "height_m": pb.z_b - pb.z_a, "n_z": pb.n_z,
+         "n_fft": 2 * pb.n_z, "screens": pb.n_screens, "screen_dx_m": pb.dx,
+         "range_m": pb.dx * pb.n_screens, "theta_max_deg": round(float(np.degrees(pb.theta_max)), 3),
+         "ray_stride": pb.ray_stride, "rk4_steps": pb.rk4_steps, "bc": "neumann",
+         "profile": "trilinear M, seed 2", "l2_between_steps": "flushed (256 MiB write)"}
+    if extra:
+        d.update(extra)
+    return d
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample
+# ---------------------------------------------------------------------------
+def oracle_sample_time(pb, stride=ORACLE_MODE_STRIDE):
+    """Seconds for one oracle screen over every stride-th mode, and the modes."""
+    from oracle.swkb_oracle import Oracle
+    o = Oracle(pb)
+    o.n = o.n[::stride]
+    o.kappa = o.kappa[::stride]
+    u = o.extend(pb.u0)
+    t = time.perf_counter()
+    o.screen(u, 0)
+    return time.perf_counter() - t, len(o.n), o.g.M
+
+
+def cpu_baseline(pb, steps=1):
+    ts = []
+    for _ in range(steps):
+        dt, m_used, m_all = oracle_sample_time(pb)
+        ts.append(dt * m_all / m_used)
+    t_screen = statistics.mean(ts)
+    return {"value": pb.n_z / t_screen, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"1 screen of the same workload over every {ORACLE_MODE_STRIDE}th mode "
+                      f"({m_used} of {m_all}), time scaled by {m_all}/{m_used} (cost is linear "
+                      f"in the mode count); numpy FP64, single thread"}
+
+
+def run_reference(args, rank, world):
+    pb = workload()
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        oracle_sample_time(pb)
+    ts, raw = [], []
+    for _ in range(args.steps):
+        dt, m_used, m_all = oracle_sample_time(pb)
+        raw.append(dt)
+        ts.append(dt * m_all / m_used)
+    t_screen = statistics.mean(ts)
+    value = pb.n_z / t_screen
+    line = {"impl": "reference", "metric": METRIC.replace("mixed FP32/FP64 path", "CPU oracle"),
+            "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": statistics.mean(raw) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(pb, {"sample_screens_per_step": 1}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step: 1 screen over every {ORACLE_MODE_STRIDE}th "
+                                       f"mode, scaled by the mode count"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+class Clocks:
+    def __init__(self, index):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
+                                 else ".", f".clocks_{os.getpid()}.csv")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={SMI_FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 8:
+                rows.append(parts)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        if not rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[0]) for r in rows if num(r[0]) is not None]
+        mx = [num(r[1]) for r in rows if num(r[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower() == "active"})
+        load = [v for v in sm if mx and v >= 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(load) if load else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def march_flops_per_ray(pb):
+    # algorithmic flops of one ray (FMA = 2): per RK4 stage the medium
+    # (quintic value + 2 derivatives, interval lookup, reflection: 39) and the
+    # x-form right-hand side of the ray and variational system (33), plus the
+    # RK4 combination (15); launch / landing evaluations and the amplitude (100)
+    return 4 * pb.rk4_steps * (39 + 33 + 15) + 100
+
+
+def resum_flops_per_term():
+    # Newton-form interpolation of phase and amplitude (15), exact integer
+    # phase + reduction (5), sincos (2), complex multiply-accumulate (10)
+    return 32
+
+
+def kernel_traffic(kind):
+    """DRAM bytes per launch from the committed ncu summary, when it was taken
+    on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    src = os.path.join(ROOT, "paper_2301_03814_gb300", "csrc", "swkb_kernels.cu")
+    try:
+        rec = json.load(open(path))
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if rec.get("kernels_sha256_16") != digest:
+            return None
+        return rec.get("bytes_per_launch", {}).get(kind)
+    except (OSError, ValueError):
+        return None
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_2301_03814_gb300 import swkb
+    from oracle.swkb_oracle import rel_l2
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    pb = workload()
+    stream = torch.cuda.Stream(device=dev)
+    plan = swkb.Plan(pb, swkb.SWKB_MIXED, stream=stream.cuda_stream, device=local)
+    plan64 = swkb.Plan(pb, swkb.SWKB_FP64, stream=stream.cuda_stream, device=local)
+    u0 = torch.from_numpy(pb.u0).to(dev)
+    out = torch.empty_like(u0)
+    out64 = torch.empty_like(u0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def timed(p, dst, steps):
+        ts = []
+        for _ in range(steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            p.propagate_device(u0.data_ptr(), dst.data_ptr())
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return ts
+
+    for _ in range(max(args.warmup, 0)):
+        plan.propagate_device(u0.data_ptr(), out.data_ptr())
+    plan64.propagate_device(u0.data_ptr(), out64.data_ptr())
+
+    clocks = Clocks(local)
+    plan.set_timing(True)
+    torch.cuda.synchronize()
+    barrier()
+    ts = timed(plan, out, args.steps)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    st = plan.stats()
+    plan.set_timing(False)
+
+    t_total = sum(ts) / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total = float(tt.item())
+    points_per_step = pb.n_z * pb.n_screens
+    value = points_per_step * args.steps * world / t_total
+
+    # FP64 path (fewer steps), same workload
+    plan64.set_timing(True)
+    ts64 = timed(plan64, out64, max(1, args.fp64_steps))
+    st64 = plan64.stats()
+    plan64.set_timing(False)
+    value64 = points_per_step * len(ts64) * world / (sum(ts64) / 1e3)
+    err = rel_l2(out.cpu().numpy(), out64.cpu().numpy())
+
+    # end to end through the C ABI with pinned host buffers
+    h_in = torch.from_numpy(pb.u0).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    n_e2e = max(1, min(args.steps, 5))
+    plan.propagate(h_in.numpy())
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        swkb.swkb_propagate(plan.handle, h_in.numpy(), 0, pb.n_screens, h_out.numpy(), 0, 0)
+    t_e2e = (time.perf_counter() - t0) / n_e2e
+    e2e = {"value": points_per_step * world / t_e2e, "unit": UNIT,
+           "h2d_bytes_per_step": int(h_in.numel() * 16), "d2h_bytes_per_step": int(h_out.numel() * 16)}
+
+    # roofline of the dominant kernel (live event times of the timed region)
+    kms = st["kernel_ms"]
+    kl = st["kernel_launches"]
+    dom = max(("march", "resum", "fft", "reduce", "bracket"), key=lambda k: kms[k])
+    info = plan.info
+    peak_fp32 = 152 * 128 * 2 * 2.07e9 / 1e12
+    if dom == "march":
+        work = march_flops_per_ray(pb) * info.n_modes * info.n_rays_total
+    elif dom == "resum":
+        work = resum_flops_per_term() * info.n_modes * info.n_fft
+    else:
+        work = None
+    roofline = None
+    if work is not None and kl[dom]:
+        per_launch_s = kms[dom] / 1e3 / kl[dom]
+        achieved = work / per_launch_s / 1e12
+        roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_fp32,
+                    "unit": "TFLOP/s", "frac": achieved / peak_fp32,
+                    "traffic": kernel_traffic(dom),
+                    "peak_source": f"derived: {FP32_PEAK_NOTE}",
+                    "work_per_launch": work, "launch_ms": per_launch_s * 1e3}
+    share = {k: round(v / max(sum(kms.values()), 1e-30), 4) for k, v in kms.items()}
+
+    if rank != 0:
+        return 0
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": statistics.mean(ts), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 range-phase carry)",
+            "data": "synthetic",
+            "config": config_dict(pb, {"parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
+            "e2e": e2e, "gpu_launches": int(st["launches"]),
+            "fp64": {"value": value64, "unit": UNIT, "ms_per_step": statistics.mean(ts64),
+                     "steps": len(ts64), "kernel_ms_per_step": {k: v / len(ts64) for k, v in st64["kernel_ms"].items()}},
+            "mixed_vs_fp64_rel_l2": err,
+            "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
+            "kernel_share": share, "roofline": roofline, "clocks": clk,
+            "step_ms": {"p50": statistics.median(ts), "p99": float(np.percentile(ts, 99)),
+                        "min": min(ts), "max": max(ts)}}
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(pb)
+    print(json.dumps(line), flush=True)
+    plan.close()
+    plan64.close()
+    return 0
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

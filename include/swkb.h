@@ -1,0 +1,248 @@
+/*
+ * swkb.h -- C ABI of libswkb.so, a single-GPU (sm_103a) screened-WKB
+ * propagator (Bruno & Maas, "WKB Across Caustics: The Screened-WKB Method").
+ *
+ * The library advances a 2-D Helmholtz field u(x, z) of the model problem
+ * Laplace(u) + k^2 eps(x, z) u = 0 (Sec. 2, Eq. helmholtz_3D) from one flat
+ * screen x = x_q to the next (Sec. 2, Eq. ray_bundle; Algorithm 1):
+ *   (a) DFT of the screen field into plane-wave modes (Eqs. fft_eq, ifft_eq,
+ *       fourier_psi), keeping |n| <= n_max;
+ *   (b) each mode's ray family marched across the slab by classical RK4 on the
+ *       characteristics of the eikonal / transport equations (Eqs. charsys,
+ *       charsys_s, transport_xt) with x as the ray parameter; the amplitude is
+ *       A = A0 sqrt(P0 / (P1 Z_s)), the corrected form of Eq.
+ *       delta_psi_eq_jac (J = X_t Z_s - Z_t X_s, Delta psi = J_t / (2 J));
+ *   (c) 4-point Lagrange interpolation of each mode's phase and amplitude from
+ *       the ray landings onto the grid of the next screen (Eq.
+ *       ray_bundle_q_plus_1);
+ *   (d) the modal sum u(z_m) = sum_n A_n(z_m) exp(i k psi_n(z_m)).
+ * Ground boundaries (Neumann / Dirichlet) use the paper's reflection (Sec.
+ * 2.3): the library solves on the mirrored period and projects the field onto
+ * even / odd functions after each screen.
+ *
+ * Conventions for every entry point:
+ *   - No C++ exception crosses this boundary; every call returns swkb_status.
+ *     On failure a message is available from swkb_last_error() (thread-local).
+ *   - Inputs passed by pointer are copied before the call returns; the caller
+ *     keeps ownership.  Outputs are written only when the call returns SWKB_OK
+ *     (device outputs may have been overwritten in part on error).
+ *   - Complex fields are complex128, interleaved (re, im) doubles.  A field on
+ *     n_z points holds the values at z_m = z_a + m (z_b - z_a) / n_z,
+ *     m = 0 .. n_z - 1 (for grounded domains: the physical half z >= z_a).
+ *   - A plan is not thread-safe; use one plan per host thread.  The server
+ *     (swkb_server_*) is thread-safe.
+ *   - No entry point forks, traps or spins without a bound.
+ */
+#ifndef SWKB_H
+#define SWKB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct swkb_plan swkb_plan;      /* opaque, library-owned */
+typedef struct swkb_server swkb_server;  /* opaque, library-owned */
+
+typedef enum {
+  SWKB_OK = 0,
+  SWKB_ERR_INVALID_ARG = 1,  /* bad argument; nothing was changed            */
+  SWKB_ERR_OOM = 2,          /* device memory could not be allocated          */
+  SWKB_ERR_CAUSTIC = 3,      /* a ray family folded between two screens:
+                                Z_s <= 0 or ray landings not increasing (the
+                                Remark after Eq. ray_bundle_q_plus_1: choose a
+                                smaller screen spacing)                      */
+  SWKB_ERR_TURNING = 4,      /* eps - Q^2 <= 0 on a ray (turning point in x) */
+  SWKB_ERR_RANGE = 5,        /* a ray left the permittivity table, or the
+                                ghost rays did not cover the screen          */
+  SWKB_ERR_CUDA = 6,         /* a CUDA runtime call failed                   */
+  SWKB_ERR_TIMEOUT = 7,      /* a bounded wait gave up                       */
+  SWKB_ERR_AGAIN = 8,        /* server queue full; retry later               */
+  SWKB_NOT_READY = 9,        /* swkb_poll: request still in flight           */
+  SWKB_ERR_CANCELLED = 10    /* request cancelled                            */
+} swkb_status;
+
+enum { SWKB_BC_PERIODIC = 0, SWKB_BC_NEUMANN = 1, SWKB_BC_DIRICHLET = 2 };
+enum { SWKB_FP64 = 0, SWKB_MIXED = 1 };
+
+/*
+ * Permittivity eps(x, z) = n(x, z)^2 and its first two z-derivatives, sampled
+ * on n_cols range columns x_cols[c] (non-decreasing; two equal positions
+ * encode a jump: left limit first, then right limit) and n_p uniform nodes
+ * z0_p + i dz_p.  Arrays are row-major [n_cols][n_p] float64, caller-owned,
+ * copied by swkb_plan_create.  The library evaluates eps by quintic Hermite
+ * interpolation in z (C^2) and linearly in x between the columns that bracket
+ * x; at the start of a screen the right limit is taken, at its end the left.
+ * For grounded domains (SWKB_BC_NEUMANN / _DIRICHLET) the table describes
+ * z >= z_a only, must start at z0_p == z_a and must have eps_z == 0 there;
+ * the library evaluates the reflected permittivity eps(z_a + |z - z_a|)
+ * (Sec. 2.3).
+ */
+typedef struct {
+  int32_t n_cols;
+  const double* x_cols;
+  int32_t n_p;
+  double z0_p, dz_p;
+  const double* eps;
+  const double* eps_z;
+  const double* eps_zz;
+} swkb_profile;
+
+/* Physical vertical extent [z_a, z_b), first screen x0, boundary condition. */
+typedef struct {
+  double z_a, z_b, x0;
+  int32_t bc;
+} swkb_domain;
+
+typedef struct {
+  int32_t precision;      /* SWKB_FP64 or SWKB_MIXED (FP32 arithmetic with an
+                             FP64 range-phase carry)                          */
+  double theta_max;       /* radians; keeps |n| <= floor(sin(theta_max) L/lambda) */
+  int32_t n_max;          /* > 0 overrides theta_max                          */
+  int32_t ray_stride;     /* R: one ray every R grid points (R | N_fft)       */
+  int32_t rk4_steps;      /* N_t: RK4 steps per screen                        */
+  double absorber_frac;   /* top absorber over this fraction of the height
+                             (grounded domains only; 0 = off)                  */
+  int32_t autotune;       /* 1: time candidate tilings at plan creation       */
+  void* cuda_stream;      /* cudaStream_t to run on; NULL = a library stream  */
+  int32_t device;         /* CUDA device ordinal                              */
+} swkb_options;
+
+typedef struct {
+  int32_t n_fft;          /* N: period points (n_z, or 2 n_z when grounded)   */
+  int32_t n_max, n_modes; /* kept modes n = -n_max .. n_max                   */
+  int32_t n_rays;         /* N / R                                            */
+  int32_t n_ghost;        /* ghost rays per side                              */
+  int32_t n_rays_total;   /* n_rays + 2 n_ghost (per mode)                    */
+  int32_t tile_points;    /* grid points per resummation tile                 */
+  int32_t mode_groups;    /* mode groups of the resummation                   */
+  double dz, period;      /* grid spacing, period length                      */
+  double eps_ref;         /* reference permittivity of the phase carry        */
+  size_t device_bytes;    /* device memory held by the plan                   */
+} swkb_plan_info;
+
+/* Fill *opt with defaults: FP64, theta_max 30 deg, R 1, N_t 8, no absorber. */
+void swkb_options_default(swkb_options* opt);
+
+/*
+ * Build a plan: validates the arguments, derives the mode set and the ray
+ * layout, uploads the permittivity table and allocates every device buffer
+ * (all allocation happens here).  n_z physical points; screen_dx the screen
+ * spacing.  The FFT length (n_z, or 2 n_z when grounded) must be a power of
+ * two between 64 and 2^20.  Returns SWKB_ERR_INVALID_ARG on bad shapes, on a
+ * table that does not cover the rays' reach, or on a mode evanescent at the
+ * reference permittivity.
+ */
+swkb_status swkb_plan_create(const swkb_profile* profile, double k, const swkb_domain* domain,
+                             int32_t n_z, double screen_dx, const swkb_options* options,
+                             swkb_plan** out);
+
+swkb_status swkb_plan_get_info(const swkb_plan* plan, swkb_plan_info* info);
+
+/*
+ * Propagate: u0 on screen q0 (x = x0 + q0 dx) -> u_out on screen
+ * q0 + n_screens.  u0 / u_out hold n_z complex128 values; with on_device = 0
+ * they are host pointers (the library copies in and out), with on_device = 1
+ * device pointers on the plan's stream.  When snapshot_every > 0, u_out holds
+ * n_screens / snapshot_every consecutive fields (after screens q0 +
+ * snapshot_every, q0 + 2 snapshot_every, ...) instead of the last one only.
+ * Restarting from a returned field at the matching q0 gives the same result
+ * as one longer call (checkpoint / resume).  Blocks until the plan's stream
+ * has finished (the status of every ray is read back).
+ */
+swkb_status swkb_propagate(swkb_plan* plan, const double* u0, int32_t q0, int32_t n_screens,
+                           double* u_out, int32_t snapshot_every, int32_t on_device);
+
+/*
+ * One screen with every intermediate exposed, for testing (host pointers;
+ * any output may be NULL).  u_full: N complex128 values on the whole period
+ * (z_lo + m dz; z_lo = 2 z_a - z_b when grounded).  Outputs: c [n_modes]
+ * complex128 mode coefficients w_n / N (step a); delta, r, a [n_modes]
+ * [n_rays_total] float64 ray landing (grid units from z_lo), residual phase
+ * r = psi - kappa_n (z - z_lo) and amplitude factor sqrt(P0 / (P1 Z_s))
+ * (step b); u_next N complex128: the modal sum times the absorber, before the
+ * reflection step (steps c, d).
+ */
+swkb_status swkb_debug_screen(swkb_plan* plan, int32_t q, const double* u_full, double* c,
+                              double* delta, double* r, double* a, double* u_next);
+
+void swkb_plan_destroy(swkb_plan* plan);
+
+/* Kernel kinds of the per-kernel accounting (swkb_plan_stats). */
+enum {
+  SWKB_KERNEL_INIT = 0,     /* field -> full period (extension)              */
+  SWKB_KERNEL_REDUCE = 1,   /* partial sums, absorber, reflection            */
+  SWKB_KERNEL_FFT = 2,      /* step (a), both FFT passes                     */
+  SWKB_KERNEL_MARCH = 3,    /* step (b)                                      */
+  SWKB_KERNEL_BRACKET = 4,  /* landing checks, tile brackets                 */
+  SWKB_KERNEL_RESUM = 5,    /* steps (c) + (d)                               */
+  SWKB_KERNEL_OUTPUT = 6,   /* full period -> n_z complex128                 */
+  SWKB_KERNEL_KINDS = 7
+};
+
+typedef struct {
+  uint64_t launches;                         /* kernel launches since reset    */
+  uint64_t screens;                          /* screens advanced since reset   */
+  uint64_t kernel_launches[SWKB_KERNEL_KINDS];
+  double kernel_ms[SWKB_KERNEL_KINDS];       /* device time per kind, from CUDA
+                                                events recorded on the plan's
+                                                stream around each launch (only
+                                                while timing is on)            */
+} swkb_plan_stats;
+
+/* on = 1: record CUDA events around every kernel launch of this plan (on its
+   stream) and accumulate per-kind device time; on = 0: stop.  Both reset the
+   counters. */
+swkb_status swkb_plan_set_timing(swkb_plan* plan, int32_t on);
+swkb_status swkb_plan_get_stats(const swkb_plan* plan, swkb_plan_stats* stats);
+
+/* ---------------------------------------------------------------------------
+ * Serving: a continuous-batching request loop.  Requests (each a whole
+ * propagation job) are admitted while their device footprint fits the HBM
+ * budget and a slot is free; every admitted request keeps its field and ray
+ * state resident on the device and advances one screen per scheduler round,
+ * interleaved with the other resident requests on separate streams, so that
+ * requests of different sizes overlap on the GPU.  Arrivals wait in a FIFO.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  const swkb_profile* profile;
+  double k;
+  const swkb_domain* domain;
+  int32_t n_z;
+  double screen_dx;
+  const swkb_options* options;  /* cuda_stream is ignored (the server owns streams) */
+  const double* u0;             /* host, n_z complex128, copied at submit     */
+  int32_t q0, n_screens;
+} swkb_request;
+
+typedef struct {
+  uint64_t submitted, completed, failed, rejected;
+  int32_t resident, queued;
+  size_t hbm_in_use;
+} swkb_server_stats;
+
+/* hbm_budget_bytes: device bytes the resident requests may hold; max_slots:
+   requests resident at once; queue_cap: waiting requests (0 = unbounded). */
+swkb_status swkb_server_create(size_t hbm_budget_bytes, int32_t max_slots, int32_t queue_cap,
+                               int32_t device, swkb_server** out);
+/* Copies the request; SWKB_ERR_AGAIN when the queue is full; *ticket > 0. */
+swkb_status swkb_submit(swkb_server* server, const swkb_request* req, uint64_t* ticket);
+/* SWKB_NOT_READY while in flight; on completion copies the n_z complex128
+   result to host u_out (may be NULL) and releases the ticket; a failed
+   request returns its error status once.  timeout_ms < 0 waits without
+   limit, 0 polls. */
+swkb_status swkb_poll(swkb_server* server, uint64_t ticket, double* u_out, int32_t timeout_ms);
+swkb_status swkb_cancel(swkb_server* server, uint64_t ticket);
+swkb_status swkb_server_get_stats(swkb_server* server, swkb_server_stats* stats);
+/* Cancels queued requests, waits for resident ones, frees everything. */
+void swkb_server_destroy(swkb_server* server);
+
+const char* swkb_last_error(void);
+const char* swkb_status_string(swkb_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SWKB_H */

@@ -396,7 +396,7 @@ class Oracle:
         delta = (rays["z"] - g.z_lo) / g.dz
         m = np.arange(g.N)
         out = np.zeros(g.N, dtype=np.complex128)
-        for i in range(g.M):                                         # (c) + (d)
+        for i in range(len(self.n)):                                 # (c) + (d)
             r_m, a_m = self.interpolate(delta[i], (rays["r"][i], rays["a"][i]))
             n = int(self.n[i])
             base = 2.0 * math.pi * ((n * m) % g.N) / g.N             # = k kappa_n (z_m - z_lo)

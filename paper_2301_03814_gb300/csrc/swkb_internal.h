@@ -1,0 +1,115 @@
+// Internal declarations shared by the kernel and host translation units of
+// libswkb.so.  Nothing here is part of the public C ABI (include/swkb.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace swkb {
+
+// Status bits written by device code (atomicOr) and mapped to swkb_status.
+enum : unsigned {
+  ST_CAUSTIC = 1u,   // Z_s <= 0 or landings not increasing
+  ST_TURNING = 2u,   // eps - Q^2 <= 0
+  ST_RANGE = 4u,     // left the permittivity table
+  ST_COVER = 8u,     // ghost rays do not cover the screen
+};
+
+template <typename T> struct C2;
+template <> struct C2<float> { using type = float2; };
+template <> struct C2<double> { using type = double2; };
+
+// Quintic medium table: per column, per z interval i, the monomial
+// coefficients a0..a5 of eps(z0 + (i + t) h) - eps_ref in t in [0, 1]
+// (8 slots per interval, the last two unused).  Reflection about z_mirror for
+// grounded domains.
+template <typename T>
+struct Medium {
+  const T* coef;
+  int n_int;
+  long long col_stride;
+  T z0, inv_h, inv_h2;
+  int mirrored;
+  T z_mirror;
+};
+
+// Per-screen RK4 stage columns: stage l = 0 .. 2 N_t sits at x_q + l h / 2;
+// eps there is (1 - th) col[c] + th col[c + 1].
+template <typename T>
+struct Stages {
+  const int* c;
+  const T* th;
+};
+
+template <typename T>
+struct MarchArgs {
+  Medium<T> med;
+  Stages<T> st;
+  const T* kappa;   // [M] kappa_n
+  const T* pbar;    // [M] sqrt(eps_ref - kappa_n^2)
+  const T* pbar2;   // [M] eps_ref - kappa_n^2
+  int M, NRT, G, R, Nt;
+  T z_lo, dz, inv_dz, h, k_over_2pi;
+  T* out_d;         // [NRT][M] landing offset from the launch grid point, grid units
+  T* out_ph;        // [NRT][M] residual phase k (r - x P_bar) / (2 pi), turns
+  T* out_a;         // [NRT][M] amplitude factor sqrt(P0 / (P1 Z_s))
+  unsigned* status;
+};
+
+template <typename T>
+struct BracketArgs {
+  const T* d;       // [NRT][M]
+  int M, NRT, G, R, N, TM, n_tiles;
+  int* jlo;         // [n_tiles + 1][M] bracket ray of each tile start
+  unsigned* status;
+};
+
+template <typename T>
+struct ResumArgs {
+  const T* d;
+  const T* ph;
+  const T* a;
+  const int* jlo;
+  const typename C2<T>::type* c;   // [M] mode coefficients, range phase folded in
+  int M, NRT, G, R, N, TM, PW, n_tiles, n_groups, modes_per_group, n_max, wcap;
+  typename C2<T>::type* part;      // [n_groups][N]
+  unsigned* status;
+};
+
+template <typename T>
+struct ReduceArgs {
+  const typename C2<T>::type* part;  // [n_part][N]
+  int n_part, N;
+  const T* W;                        // [N] absorber or nullptr
+  int mirror;                        // 0 none, +1 even, -1 odd
+  typename C2<T>::type* u;           // [N]
+};
+
+template <typename T>
+struct FftArgs {
+  const typename C2<T>::type* u;     // [N]
+  const typename C2<T>::type* tw;    // [N] exp(-2 pi i k / N)
+  typename C2<T>::type* Y;           // [N1][N2]
+  int N, N1, N2, log2N2, n_max;
+  T inv_N;
+  const typename C2<T>::type* ephi;  // [M] exp(i Phi_n)
+  typename C2<T>::type* c;           // [M]
+};
+
+// launchers (defined in swkb_kernels.cu for T = float, double)
+template <typename T> cudaError_t launch_init(const double* u0, int n_z, int N, int mirror,
+                                              typename C2<T>::type* u, cudaStream_t s);
+template <typename T> cudaError_t launch_reduce(const ReduceArgs<T>& a, cudaStream_t s);
+template <typename T> cudaError_t launch_fft(const FftArgs<T>& a, cudaStream_t s);
+template <typename T> cudaError_t launch_march(const MarchArgs<T>& a, cudaStream_t s);
+template <typename T> cudaError_t launch_bracket(const BracketArgs<T>& a, cudaStream_t s);
+template <typename T> cudaError_t launch_resum(const ResumArgs<T>& a, int warps_per_cta,
+                                               cudaStream_t s);
+template <typename T> cudaError_t launch_output(const typename C2<T>::type* u, int offset, int n,
+                                                double* out, cudaStream_t s);
+template <typename T> size_t resum_smem_bytes(int wcap, int warps_per_cta);
+// Raise the dynamic shared-memory limits of the FFT and resummation kernels
+// on the current device (call once per device before launching).
+template <typename T> cudaError_t prepare_kernels(int resum_smem);
+
+}  // namespace swkb

@@ -1,0 +1,749 @@
+// Host side of libswkb.so: plan construction (mode set, ray layout, medium
+// tables, device buffers), the screen loop, and the C ABI of include/swkb.h.
+//
+// Everything the device path needs in FP64 is prepared here:
+//   - the medium table as per-interval quintic coefficients of eps - eps_ref
+//     (quintic Hermite in z from eps, eps_z, eps_zz; reading of the paper's
+//     silent medium representation), cast to FP32 for the mixed path;
+//   - the per-screen RK4 stage columns (linear in x, right limit at the start
+//     of a screen and left limit at its end);
+//   - the mode table kappa_n = 2 pi n / (k L) (Eq. fourier_psi with the
+//     origin at the bottom of the period), P_bar_n = sqrt(eps_ref - kappa_n^2)
+//     and the range-phase carry exp(i k dx P_bar_n) (reduced mod 2 pi in FP64);
+//   - DFT twiddles and the top absorber window.
+
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "swkb.h"
+#include "swkb_internal.h"
+
+using namespace swkb;
+
+namespace {
+
+thread_local std::string g_err;
+
+swkb_status fail(swkb_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define CK(call)                                                                            \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return fail(SWKB_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),    \
+                  __FILE__, __LINE__);                                                      \
+  } while (0)
+
+bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int ilog2(long long v) {
+  int l = 0;
+  while ((1LL << l) < v) ++l;
+  return l;
+}
+
+}  // namespace
+
+struct swkb_plan {
+  // problem
+  int precision = SWKB_FP64;
+  int bc = SWKB_BC_PERIODIC;
+  int mirror = 0;  // 0 periodic, +1 Neumann, -1 Dirichlet
+  int n_z = 0, N = 0, N1 = 1, N2 = 1, log2N2 = 0;
+  int n_max = 0, M = 0, R = 1, N_r = 0, G = 0, NRT = 0, Nt = 0;
+  double k = 0, z_a = 0, z_b = 0, x0 = 0, dx = 0, L = 0, dz = 0, z_lo = 0;
+  double eps_ref = 0, absorber_frac = 0;
+  // resummation tiling
+  int PW = 8, TM = 256, n_tiles = 0, n_groups = 1, modes_per_group = 1, wcap = 0;
+  int warps_per_cta = 4;
+  // medium
+  int n_cols = 0, n_p = 0, n_int = 0;
+  double z0p = 0, dzp = 0;
+  std::vector<double> x_cols;
+  int stage_rows = 1;  // screens q >= stage_rows - 1 share the last row
+  std::vector<double> pbar;  // host copy of P_bar_n (FP64)
+  std::vector<double> ephi;  // exp(i k dx P_bar_n), interleaved
+  // device
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  void* coef = nullptr;
+  void* tw = nullptr;
+  void* W = nullptr;
+  void* kappa = nullptr;
+  void* pbar_d = nullptr;
+  void* pbar2_d = nullptr;
+  void* ephi_d = nullptr;
+  void* u = nullptr;
+  void* part = nullptr;
+  void* Y = nullptr;
+  void* c = nullptr;
+  void* rd = nullptr;
+  void* rph = nullptr;
+  void* ra = nullptr;
+  int* jlo = nullptr;
+  unsigned* status = nullptr;
+  int* stage_c = nullptr;
+  void* stage_th = nullptr;
+  double* io = nullptr;  // complex128 staging, max(N, n_z) values
+  size_t bytes = 0;
+  std::vector<void*> allocs;
+  // accounting
+  swkb_plan_stats stats{};
+  bool timing = false;
+  std::vector<cudaEvent_t> events;   // pool, reused every run
+  struct Mark { int kind; int e0, e1; };
+  std::vector<Mark> marks;           // pending, harvested after a sync
+};
+
+namespace {
+
+swkb_status dev_alloc(swkb_plan* p, void** ptr, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(SWKB_ERR_OOM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+  }
+  p->allocs.push_back(*ptr);
+  p->bytes += bytes;
+  return SWKB_OK;
+}
+
+#define TRY(x)                      \
+  do {                              \
+    swkb_status s_ = (x);           \
+    if (s_ != SWKB_OK) return s_;   \
+  } while (0)
+
+// Columns (c, c + 1) and weight th of column c + 1 at range x.  right: take
+// the right limit at a column position (x_cols[c] <= x), else the left one.
+void column_weights(const std::vector<double>& xc, double x, bool right, int* c, double* th) {
+  const int n = (int)xc.size();
+  if (n == 1) { *c = 0; *th = 0.0; return; }
+  int cnt = 0;
+  for (int i = 0; i < n; ++i) cnt += right ? (xc[i] <= x) : (xc[i] < x);
+  int cc = std::min(std::max(cnt - 1, 0), n - 2);
+  const double span = xc[cc + 1] - xc[cc];
+  double t = span <= 0 ? 0.0 : (x - xc[cc]) / span;
+  *c = cc;
+  *th = std::min(std::max(t, 0.0), 1.0);
+}
+
+template <typename T>
+swkb_status upload(swkb_plan* p, void** dst, const std::vector<double>& v) {
+  std::vector<T> tmp(v.begin(), v.end());
+  TRY(dev_alloc(p, dst, tmp.size() * sizeof(T)));
+  CK(cudaMemcpy(*dst, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return SWKB_OK;
+}
+
+swkb_status status_from_bits(unsigned bits) {
+  if (bits & ST_CAUSTIC)
+    return fail(SWKB_ERR_CAUSTIC,
+                "caustic between screens (Z_s <= 0 or ray landings out of order); "
+                "use a smaller screen spacing");
+  if (bits & ST_TURNING) return fail(SWKB_ERR_TURNING, "turning point on a ray (eps - Q^2 <= 0)");
+  if (bits & ST_RANGE) return fail(SWKB_ERR_RANGE, "a ray left the permittivity table");
+  if (bits & ST_COVER) return fail(SWKB_ERR_RANGE, "ghost rays do not cover the screen");
+  return SWKB_OK;
+}
+
+template <typename T>
+swkb_status build_device(swkb_plan* p, const swkb_profile* prof) {
+  using V = typename C2<T>::type;
+  const int M = p->M, N = p->N;
+  // medium coefficient table (eps - eps_ref), 8 slots per interval
+  {
+    std::vector<double> coef((size_t)p->n_cols * p->n_int * 8, 0.0);
+    const double h = p->dzp;
+    for (int c = 0; c < p->n_cols; ++c) {
+      const double* e = prof->eps + (size_t)c * p->n_p;
+      const double* ez = prof->eps_z + (size_t)c * p->n_p;
+      const double* ezz = prof->eps_zz + (size_t)c * p->n_p;
+      for (int i = 0; i < p->n_int; ++i) {
+        const double f0 = e[i] - p->eps_ref, f1 = e[i + 1] - p->eps_ref;
+        const double a0 = f0, a1 = h * ez[i], a2 = 0.5 * h * h * ezz[i];
+        const double A = f1 - a0 - a1 - a2;
+        const double B = h * ez[i + 1] - a1 - 2.0 * a2;
+        const double C = h * h * ezz[i + 1] - 2.0 * a2;
+        double* o = coef.data() + ((size_t)c * p->n_int + i) * 8;
+        o[0] = a0; o[1] = a1; o[2] = a2;
+        o[3] = 10.0 * A - 4.0 * B + 0.5 * C;
+        o[4] = -15.0 * A + 7.0 * B - C;
+        o[5] = 6.0 * A - 3.0 * B + 0.5 * C;
+      }
+    }
+    TRY(upload<T>(p, &p->coef, coef));
+  }
+  // RK4 stage columns for screens 0 .. stage_rows - 1
+  {
+    const int S = 2 * p->Nt + 1;
+    std::vector<int> sc((size_t)p->stage_rows * S);
+    std::vector<double> st((size_t)p->stage_rows * S);
+    const double h = p->dx / p->Nt;
+    for (int q = 0; q < p->stage_rows; ++q) {
+      const double xq = p->x0 + q * p->dx;
+      const double xn = p->x0 + (q + 1) * p->dx;
+      for (int l = 0; l < S; ++l) {
+        const bool last = (l == S - 1);
+        const double x = last ? xn : xq + 0.5 * l * h;
+        int c;
+        double th;
+        column_weights(p->x_cols, x, !last, &c, &th);
+        sc[(size_t)q * S + l] = c;
+        st[(size_t)q * S + l] = th;
+      }
+    }
+    TRY(dev_alloc(p, (void**)&p->stage_c, sc.size() * sizeof(int)));
+    CK(cudaMemcpy(p->stage_c, sc.data(), sc.size() * sizeof(int), cudaMemcpyHostToDevice));
+    TRY(upload<T>(p, &p->stage_th, st));
+  }
+  // modes
+  {
+    std::vector<double> kap(M), pb(M), pb2(M);
+    p->pbar.assign(M, 0.0);
+    p->ephi.assign(2 * (size_t)M, 0.0);
+    for (int i = 0; i < M; ++i) {
+      const int n = i - p->n_max;
+      kap[i] = 2.0 * M_PI * n / (p->k * p->L);
+      pb2[i] = p->eps_ref - kap[i] * kap[i];
+      pb[i] = sqrt(pb2[i]);
+      p->pbar[i] = pb[i];
+      const double phi = fmod(p->k * p->dx * pb[i], 2.0 * M_PI);
+      p->ephi[2 * i] = cos(phi);
+      p->ephi[2 * i + 1] = sin(phi);
+    }
+    TRY(upload<T>(p, &p->kappa, kap));
+    TRY(upload<T>(p, &p->pbar_d, pb));
+    TRY(upload<T>(p, &p->pbar2_d, pb2));
+    TRY(upload<T>(p, &p->ephi_d, p->ephi));
+  }
+  // twiddles exp(-2 pi i k / N)
+  {
+    std::vector<double> tw(2 * (size_t)N);
+    for (int k = 0; k < N; ++k) {
+      const double a = 2.0 * M_PI * ((double)k / N);
+      tw[2 * k] = cos(a);
+      tw[2 * k + 1] = -sin(a);
+    }
+    TRY(upload<T>(p, &p->tw, tw));
+  }
+  // absorber
+  if (p->absorber_frac > 0) {
+    std::vector<double> w(N, 1.0);
+    const double H = p->z_b - p->z_a, f = p->absorber_frac;
+    for (int m = 0; m < N; ++m) {
+      const double z = p->z_lo + p->dz * m;
+      const double d = p->mirror ? fabs(z - p->z_a) : (z - p->z_a);
+      if (d > (1.0 - f) * H) {
+        const double cth = cos(0.5 * M_PI * (d - (1.0 - f) * H) / (f * H));
+        w[m] = cth * cth;
+      }
+    }
+    TRY(upload<T>(p, &p->W, w));
+  }
+  // work buffers
+  TRY(dev_alloc(p, &p->u, (size_t)N * sizeof(V)));
+  TRY(dev_alloc(p, &p->part, (size_t)p->n_groups * N * sizeof(V)));
+  TRY(dev_alloc(p, &p->Y, (size_t)N * sizeof(V)));
+  TRY(dev_alloc(p, &p->c, (size_t)M * sizeof(V)));
+  TRY(dev_alloc(p, &p->rd, (size_t)p->NRT * M * sizeof(T)));
+  TRY(dev_alloc(p, &p->rph, (size_t)p->NRT * M * sizeof(T)));
+  TRY(dev_alloc(p, &p->ra, (size_t)p->NRT * M * sizeof(T)));
+  TRY(dev_alloc(p, (void**)&p->jlo, (size_t)(p->n_tiles + 1) * M * sizeof(int)));
+  CK(cudaMemset(p->jlo, 0, (size_t)(p->n_tiles + 1) * M * sizeof(int)));
+  TRY(dev_alloc(p, (void**)&p->status, sizeof(unsigned)));
+  CK(cudaMemset(p->status, 0, sizeof(unsigned)));
+  TRY(dev_alloc(p, (void**)&p->io, 2 * (size_t)std::max(N, p->n_z) * sizeof(double)));
+  CK(prepare_kernels<T>((int)resum_smem_bytes<T>(p->wcap, p->warps_per_cta)));
+  return SWKB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// per-kernel accounting: launch counts always, CUDA-event timing on request
+// ---------------------------------------------------------------------------
+swkb_status event_at(swkb_plan* p, int idx) {
+  while ((int)p->events.size() <= idx) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    p->events.push_back(e);
+  }
+  return SWKB_OK;
+}
+
+template <typename F>
+swkb_status timed(swkb_plan* p, int kind, int n_launches, F&& launch) {
+  int e0 = -1, e1 = -1;
+  if (p->timing) {
+    e0 = 2 * (int)p->marks.size();
+    e1 = e0 + 1;
+    TRY(event_at(p, e1));
+    CK(cudaEventRecord(p->events[e0], p->stream));
+  }
+  CK(launch());
+  if (p->timing) {
+    CK(cudaEventRecord(p->events[e1], p->stream));
+    p->marks.push_back({kind, e0, e1});
+  }
+  p->stats.launches += n_launches;
+  p->stats.kernel_launches[kind] += n_launches;
+  return SWKB_OK;
+}
+
+// after the stream has been synchronised
+swkb_status harvest(swkb_plan* p) {
+  for (const auto& m : p->marks) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, p->events[m.e0], p->events[m.e1]));
+    p->stats.kernel_ms[m.kind] += ms;
+  }
+  p->marks.clear();
+  return SWKB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// kernel argument builders
+// ---------------------------------------------------------------------------
+template <typename T>
+MarchArgs<T> march_args(const swkb_plan* p, int q) {
+  MarchArgs<T> a;
+  a.med.coef = (const T*)p->coef;
+  a.med.n_int = p->n_int;
+  a.med.col_stride = (long long)p->n_int * 8;
+  a.med.z0 = (T)p->z0p;
+  a.med.inv_h = (T)(1.0 / p->dzp);
+  a.med.inv_h2 = (T)(1.0 / (p->dzp * p->dzp));
+  a.med.mirrored = p->mirror != 0;
+  a.med.z_mirror = (T)p->z_a;
+  const int S = 2 * p->Nt + 1;
+  const int row = std::min(std::max(q, 0), p->stage_rows - 1);
+  a.st.c = p->stage_c + (size_t)row * S;
+  a.st.th = (const T*)p->stage_th + (size_t)row * S;
+  a.kappa = (const T*)p->kappa;
+  a.pbar = (const T*)p->pbar_d;
+  a.pbar2 = (const T*)p->pbar2_d;
+  a.M = p->M; a.NRT = p->NRT; a.G = p->G; a.R = p->R; a.Nt = p->Nt;
+  a.z_lo = (T)p->z_lo; a.dz = (T)p->dz; a.inv_dz = (T)(1.0 / p->dz);
+  a.h = (T)(p->dx / p->Nt);
+  a.k_over_2pi = (T)(p->k / (2.0 * M_PI));
+  a.out_d = (T*)p->rd; a.out_ph = (T*)p->rph; a.out_a = (T*)p->ra;
+  a.status = p->status;
+  return a;
+}
+
+template <typename T>
+swkb_status launch_screen(swkb_plan* p, int q, bool u_fresh) {
+  using V = typename C2<T>::type;
+  cudaStream_t s = p->stream;
+  if (!u_fresh) {
+    ReduceArgs<T> r{(const V*)p->part, p->n_groups, p->N, (const T*)p->W, p->mirror, (V*)p->u};
+    TRY(timed(p, SWKB_KERNEL_REDUCE, 1, [&] { return launch_reduce<T>(r, s); }));
+  }
+  FftArgs<T> f;
+  f.u = (const V*)p->u; f.tw = (const V*)p->tw; f.Y = (V*)p->Y;
+  f.N = p->N; f.N1 = p->N1; f.N2 = p->N2; f.log2N2 = p->log2N2; f.n_max = p->n_max;
+  f.inv_N = (T)(1.0 / p->N);
+  f.ephi = (const V*)p->ephi_d; f.c = (V*)p->c;
+  TRY(timed(p, SWKB_KERNEL_FFT, p->N1 > 1 ? 2 : 1, [&] { return launch_fft<T>(f, s); }));
+  const MarchArgs<T> ma = march_args<T>(p, q);
+  TRY(timed(p, SWKB_KERNEL_MARCH, 1, [&] { return launch_march<T>(ma, s); }));
+  BracketArgs<T> b{(const T*)p->rd, p->M, p->NRT, p->G, p->R, p->N, p->TM, p->n_tiles,
+                   p->jlo, p->status};
+  TRY(timed(p, SWKB_KERNEL_BRACKET, 1, [&] { return launch_bracket<T>(b, s); }));
+  ResumArgs<T> ra;
+  ra.d = (const T*)p->rd; ra.ph = (const T*)p->rph; ra.a = (const T*)p->ra; ra.jlo = p->jlo;
+  ra.c = (const V*)p->c;
+  ra.M = p->M; ra.NRT = p->NRT; ra.G = p->G; ra.R = p->R; ra.N = p->N; ra.TM = p->TM;
+  ra.PW = p->PW; ra.n_tiles = p->n_tiles; ra.n_groups = p->n_groups;
+  ra.modes_per_group = p->modes_per_group; ra.n_max = p->n_max; ra.wcap = p->wcap;
+  ra.part = (V*)p->part; ra.status = p->status;
+  TRY(timed(p, SWKB_KERNEL_RESUM, 1, [&] { return launch_resum<T>(ra, p->warps_per_cta, s); }));
+  p->stats.screens += 1;
+  return SWKB_OK;
+}
+
+template <typename T>
+swkb_status reduce_to_u(swkb_plan* p, bool project) {
+  using V = typename C2<T>::type;
+  ReduceArgs<T> r{(const V*)p->part, p->n_groups, p->N, (const T*)p->W, project ? p->mirror : 0,
+                  (V*)p->u};
+  TRY(timed(p, SWKB_KERNEL_REDUCE, 1, [&] { return launch_reduce<T>(r, p->stream); }));
+  return SWKB_OK;
+}
+
+swkb_status read_status(swkb_plan* p) {
+  unsigned bits = 0;
+  CK(cudaMemcpyAsync(&bits, p->status, sizeof(unsigned), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  TRY(harvest(p));
+  if (bits) {
+    CK(cudaMemsetAsync(p->status, 0, sizeof(unsigned), p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+  }
+  return status_from_bits(bits);
+}
+
+// Screens q0 .. q0 + n - 1 from the n_z-point field u0 (device, complex128).
+// Each output field (the last one, or every snap-th) goes either to out_dev
+// + k n_z (device) or through the staging buffer to out_host + k n_z (host).
+template <typename T>
+swkb_status run(swkb_plan* p, const double* u0, int q0, int n, double* out_dev, double* out_host,
+                int snap) {
+  using V = typename C2<T>::type;
+  const int off = p->mirror ? p->n_z : 0;
+  const size_t nb = 2 * sizeof(double) * p->n_z;
+  TRY(timed(p, SWKB_KERNEL_INIT, 1,
+            [&] { return launch_init<T>(u0, p->n_z, p->N, p->mirror, (V*)p->u, p->stream); }));
+  bool fresh = true;
+  int k = 0;
+  auto emit = [&](int idx) -> swkb_status {
+    double* dst = out_dev ? out_dev + 2 * (size_t)idx * p->n_z : p->io;
+    TRY(timed(p, SWKB_KERNEL_OUTPUT, 1,
+              [&] { return launch_output<T>((const V*)p->u, off, p->n_z, dst, p->stream); }));
+    if (!out_dev)
+      CK(cudaMemcpyAsync(out_host + 2 * (size_t)idx * p->n_z, p->io, nb, cudaMemcpyDeviceToHost,
+                         p->stream));
+    return SWKB_OK;
+  };
+  for (int q = q0; q < q0 + n; ++q) {
+    TRY(launch_screen<T>(p, q, fresh));
+    fresh = false;
+    if (snap > 0 && (q - q0 + 1) % snap == 0) {
+      TRY(reduce_to_u<T>(p, true));
+      fresh = true;
+      TRY(emit(k++));
+    }
+  }
+  if (snap <= 0) {
+    if (!fresh) TRY(reduce_to_u<T>(p, true));
+    TRY(emit(0));
+  }
+  return read_status(p);
+}
+
+template <typename T>
+swkb_status debug_screen(swkb_plan* p, int q, const double* u_full, double* c, double* delta,
+                         double* r, double* a, double* u_next) {
+  using V = typename C2<T>::type;
+  const int N = p->N, M = p->M, NRT = p->NRT;
+  CK(cudaMemcpyAsync(p->io, u_full, 2 * sizeof(double) * N, cudaMemcpyHostToDevice, p->stream));
+  TRY(timed(p, SWKB_KERNEL_INIT, 1,
+            [&] { return launch_init<T>(p->io, N, N, 0, (V*)p->u, p->stream); }));
+  TRY(launch_screen<T>(p, q, true));
+  TRY(reduce_to_u<T>(p, false));
+  std::vector<V> hc(M), hu(N);
+  std::vector<T> hd((size_t)NRT * M), hph((size_t)NRT * M), ha((size_t)NRT * M);
+  CK(cudaMemcpyAsync(hc.data(), p->c, sizeof(V) * M, cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaMemcpyAsync(hu.data(), p->u, sizeof(V) * N, cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaMemcpyAsync(hd.data(), p->rd, sizeof(T) * hd.size(), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaMemcpyAsync(hph.data(), p->rph, sizeof(T) * hd.size(), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaMemcpyAsync(ha.data(), p->ra, sizeof(T) * hd.size(), cudaMemcpyDeviceToHost, p->stream));
+  TRY(read_status(p));
+  if (c) {
+    for (int i = 0; i < M; ++i) {   // divide out exp(i Phi_n)
+      const double er = p->ephi[2 * i], ei = p->ephi[2 * i + 1];
+      const double xr = hc[i].x, xi = hc[i].y;
+      c[2 * i] = xr * er + xi * ei;
+      c[2 * i + 1] = xi * er - xr * ei;
+    }
+  }
+  const double two_pi_over_k = 2.0 * M_PI / p->k;
+  for (int j = 0; j < NRT; ++j) {
+    for (int i = 0; i < M; ++i) {
+      const size_t src = (size_t)j * M + i, dst = (size_t)i * NRT + j;
+      if (delta) delta[dst] = (double)((long long)(j - p->G) * p->R) + (double)hd[src];
+      if (r) r[dst] = (double)hph[src] * two_pi_over_k + p->dx * p->pbar[i];
+      if (a) a[dst] = (double)ha[src];
+    }
+  }
+  if (u_next) {
+    for (int m = 0; m < N; ++m) {
+      u_next[2 * m] = hu[m].x;
+      u_next[2 * m + 1] = hu[m].y;
+    }
+  }
+  return SWKB_OK;
+}
+
+void release(swkb_plan* p) {
+  if (!p) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(p->device);
+  for (void* ptr : p->allocs) cudaFree(ptr);
+  for (cudaEvent_t e : p->events) cudaEventDestroy(e);
+  if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
+  cudaSetDevice(cur);
+  delete p;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void swkb_options_default(swkb_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->precision = SWKB_FP64;
+  o->theta_max = M_PI / 6.0;
+  o->n_max = 0;
+  o->ray_stride = 1;
+  o->rk4_steps = 8;
+  o->absorber_frac = 0.0;
+  o->autotune = 0;
+  o->cuda_stream = nullptr;
+  o->device = 0;
+}
+
+const char* swkb_last_error(void) { return g_err.c_str(); }
+
+const char* swkb_status_string(swkb_status s) {
+  switch (s) {
+    case SWKB_OK: return "ok";
+    case SWKB_ERR_INVALID_ARG: return "invalid argument";
+    case SWKB_ERR_OOM: return "out of device memory";
+    case SWKB_ERR_CAUSTIC: return "caustic between screens";
+    case SWKB_ERR_TURNING: return "turning point on a ray";
+    case SWKB_ERR_RANGE: return "ray outside the table or the screen";
+    case SWKB_ERR_CUDA: return "CUDA error";
+    case SWKB_ERR_TIMEOUT: return "timeout";
+    case SWKB_ERR_AGAIN: return "queue full";
+    case SWKB_NOT_READY: return "not ready";
+    case SWKB_ERR_CANCELLED: return "cancelled";
+  }
+  return "unknown status";
+}
+
+swkb_status swkb_plan_create(const swkb_profile* prof, double k, const swkb_domain* dom,
+                             int32_t n_z, double screen_dx, const swkb_options* opt_in,
+                             swkb_plan** out) {
+  try {
+    if (!out) return fail(SWKB_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!prof || !dom) return fail(SWKB_ERR_INVALID_ARG, "profile or domain is NULL");
+    swkb_options opt;
+    if (opt_in) opt = *opt_in; else swkb_options_default(&opt);
+    if (!(k > 0) || !std::isfinite(k)) return fail(SWKB_ERR_INVALID_ARG, "k must be > 0");
+    if (!(dom->z_b > dom->z_a)) return fail(SWKB_ERR_INVALID_ARG, "need z_b > z_a");
+    if (!(screen_dx > 0)) return fail(SWKB_ERR_INVALID_ARG, "screen spacing must be > 0");
+    if (dom->bc < SWKB_BC_PERIODIC || dom->bc > SWKB_BC_DIRICHLET)
+      return fail(SWKB_ERR_INVALID_ARG, "unknown boundary condition %d", dom->bc);
+    if (opt.precision != SWKB_FP64 && opt.precision != SWKB_MIXED)
+      return fail(SWKB_ERR_INVALID_ARG, "unknown precision %d", opt.precision);
+    if (prof->n_cols < 1 || prof->n_p < 3 || !(prof->dz_p > 0) || !prof->x_cols || !prof->eps ||
+        !prof->eps_z || !prof->eps_zz)
+      return fail(SWKB_ERR_INVALID_ARG, "malformed profile table");
+    for (int c = 1; c < prof->n_cols; ++c)
+      if (!(prof->x_cols[c] >= prof->x_cols[c - 1]))
+        return fail(SWKB_ERR_INVALID_ARG, "x_cols must be non-decreasing");
+    const size_t nt = (size_t)prof->n_cols * prof->n_p;
+    for (size_t i = 0; i < nt; ++i)
+      if (!std::isfinite(prof->eps[i]) || !std::isfinite(prof->eps_z[i]) ||
+          !std::isfinite(prof->eps_zz[i]))
+        return fail(SWKB_ERR_INVALID_ARG, "profile table has non-finite entries");
+
+    swkb_plan* p = new swkb_plan();
+    struct Guard { swkb_plan*& p; ~Guard() { if (p) release(p); } } guard{p};
+    p->precision = opt.precision;
+    p->bc = dom->bc;
+    p->mirror = dom->bc == SWKB_BC_NEUMANN ? 1 : (dom->bc == SWKB_BC_DIRICHLET ? -1 : 0);
+    p->k = k; p->z_a = dom->z_a; p->z_b = dom->z_b; p->x0 = dom->x0; p->dx = screen_dx;
+    p->n_z = n_z;
+    const double H = dom->z_b - dom->z_a;
+    p->N = p->mirror ? 2 * n_z : n_z;
+    if (n_z < 1 || !is_pow2(p->N) || p->N < 64 || p->N > (1 << 20))
+      return fail(SWKB_ERR_INVALID_ARG, "FFT length %d must be a power of two in [64, 2^20]", p->N);
+    p->L = p->mirror ? 2 * H : H;
+    p->dz = H / n_z;
+    p->z_lo = p->mirror ? dom->z_a - H : dom->z_a;
+    const double lam = 2.0 * M_PI / k;
+    if (opt.n_max > 0) p->n_max = opt.n_max;
+    else p->n_max = (int)floor(sin(opt.theta_max) * p->L / lam * (1.0 + 1e-12));
+    p->n_max = std::min(p->n_max, p->N / 2 - 1);
+    if (p->n_max < 1) return fail(SWKB_ERR_INVALID_ARG, "no propagating mode kept (n_max < 1)");
+    p->M = 2 * p->n_max + 1;
+    p->R = opt.ray_stride;
+    if (p->R < 1 || p->N % p->R) return fail(SWKB_ERR_INVALID_ARG, "ray stride must divide N");
+    p->N_r = p->N / p->R;
+    p->Nt = opt.rk4_steps;
+    if (p->Nt < 1 || p->Nt > 4096) return fail(SWKB_ERR_INVALID_ARG, "rk4_steps out of range");
+    const double kmax = p->n_max * lam / p->L;
+    if (!(kmax < 1.0)) return fail(SWKB_ERR_INVALID_ARG, "kept modes reach grazing angle");
+    const double tan_t = kmax / sqrt(1.0 - kmax * kmax);
+    p->G = (int)ceil(screen_dx * tan_t / (p->R * p->dz) - 1e-9) + 3;
+    p->NRT = p->N_r + 2 * p->G;
+    p->absorber_frac = opt.absorber_frac;
+    if (!(p->absorber_frac >= 0 && p->absorber_frac < 1))
+      return fail(SWKB_ERR_INVALID_ARG, "absorber_frac must be in [0, 1)");
+    // FFT split N = N1 N2 (N2 <= 2048 points in shared memory)
+    p->N2 = std::min(p->N, 2048);
+    p->N1 = p->N / p->N2;
+    p->log2N2 = ilog2(p->N2);
+    // medium
+    p->n_cols = prof->n_cols; p->n_p = prof->n_p; p->n_int = prof->n_p - 1;
+    p->z0p = prof->z0_p; p->dzp = prof->dz_p;
+    p->x_cols.assign(prof->x_cols, prof->x_cols + prof->n_cols);
+    const double ztop = p->z0p + p->dzp * (p->n_p - 1);
+    if (p->mirror) {
+      if (fabs(p->z0p - p->z_a) > 1e-9 * (1.0 + fabs(p->z_a)))
+        return fail(SWKB_ERR_INVALID_ARG, "grounded domains need the table to start at z_a");
+      double mx = 0;
+      for (size_t i = 0; i < nt; ++i) mx = std::max(mx, fabs(prof->eps_z[i]));
+      for (int c = 0; c < p->n_cols; ++c)
+        if (fabs(prof->eps_z[(size_t)c * p->n_p]) > 1e-12 * (1.0 + mx))
+          return fail(SWKB_ERR_INVALID_ARG, "grounded domains need eps_z = 0 at z_a");
+    }
+    {
+      const double reach = 1.5 * screen_dx * tan_t + 2.0 * p->dzp;
+      const double s_first = p->z_lo - (double)p->G * p->R * p->dz;
+      const double s_last = p->z_lo + (double)(p->NRT - 1 - p->G) * p->R * p->dz;
+      double lo = s_first - reach, hi = s_last + reach;
+      if (p->mirror) {
+        hi = p->z_a + std::max(fabs(lo - p->z_a), fabs(hi - p->z_a));
+        lo = p->z_a;
+      }
+      if (lo < p->z0p - 1e-9 || hi > ztop + 1e-9)
+        return fail(SWKB_ERR_INVALID_ARG,
+                    "permittivity table covers [%g, %g] but rays may reach [%g, %g]", p->z0p,
+                    ztop, lo, hi);
+    }
+    {
+      const double zm = 0.5 * (p->z_a + p->z_b);
+      long long im = llround((zm - p->z0p) / p->dzp);
+      im = std::min<long long>(std::max<long long>(im, 0), p->n_p - 1);
+      p->eps_ref = prof->eps[im];
+      if (!(p->eps_ref - kmax * kmax > 0))
+        return fail(SWKB_ERR_INVALID_ARG, "steepest kept mode is evanescent at eps_ref");
+    }
+    if (p->n_cols > 1) {
+      const double q_end = ceil((p->x_cols.back() - p->x0) / p->dx);
+      p->stage_rows = (int)std::min(std::max(q_end, 0.0), 1e6) + 1;
+    }
+    // resummation tiling
+    p->PW = p->R >= 8 ? 8 : (p->R >= 2 ? 4 : 2);
+    while (32 * p->PW > p->N) p->PW /= 2;
+    p->TM = 32 * p->PW;
+    p->n_tiles = p->N / p->TM;
+    p->wcap = 2 * p->TM / p->R + 8;
+    p->device = opt.device;
+    CK(cudaSetDevice(p->device));
+    int sms = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
+    const int target_warps = sms * 32;
+    p->n_groups = std::max(1, std::min(p->M, (target_warps + p->n_tiles - 1) / p->n_tiles));
+    p->modes_per_group = (p->M + p->n_groups - 1) / p->n_groups;
+    p->n_groups = (p->M + p->modes_per_group - 1) / p->modes_per_group;
+    if (opt.cuda_stream) {
+      p->stream = (cudaStream_t)opt.cuda_stream;
+    } else {
+      CK(cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking));
+      p->own_stream = true;
+    }
+    swkb_status st = p->precision == SWKB_FP64 ? build_device<double>(p, prof)
+                                               : build_device<float>(p, prof);
+    if (st != SWKB_OK) return st;
+    CK(cudaDeviceSynchronize());
+    *out = p;
+    p = nullptr;  // disarm guard
+    return SWKB_OK;
+  } catch (const std::exception& e) {
+    return fail(SWKB_ERR_OOM, "host allocation failed: %s", e.what());
+  } catch (...) {
+    return fail(SWKB_ERR_INVALID_ARG, "unexpected exception");
+  }
+}
+
+swkb_status swkb_plan_get_info(const swkb_plan* p, swkb_plan_info* info) {
+  if (!p || !info) return fail(SWKB_ERR_INVALID_ARG, "NULL argument");
+  info->n_fft = p->N;
+  info->n_max = p->n_max;
+  info->n_modes = p->M;
+  info->n_rays = p->N_r;
+  info->n_ghost = p->G;
+  info->n_rays_total = p->NRT;
+  info->tile_points = p->TM;
+  info->mode_groups = p->n_groups;
+  info->dz = p->dz;
+  info->period = p->L;
+  info->eps_ref = p->eps_ref;
+  info->device_bytes = p->bytes;
+  return SWKB_OK;
+}
+
+swkb_status swkb_propagate(swkb_plan* p, const double* u0, int32_t q0, int32_t n_screens,
+                           double* u_out, int32_t snapshot_every, int32_t on_device) {
+  try {
+    if (!p || !u0 || !u_out) return fail(SWKB_ERR_INVALID_ARG, "NULL argument");
+    if (n_screens < 0 || q0 < 0) return fail(SWKB_ERR_INVALID_ARG, "negative screen count");
+    if (snapshot_every < 0 || (snapshot_every > 0 && n_screens % snapshot_every))
+      return fail(SWKB_ERR_INVALID_ARG, "snapshot_every must divide n_screens");
+    CK(cudaSetDevice(p->device));
+    const size_t nb = 2 * sizeof(double) * p->n_z;
+    if (n_screens == 0) {
+      if (on_device) CK(cudaMemcpyAsync(u_out, u0, nb, cudaMemcpyDeviceToDevice, p->stream));
+      else memcpy(u_out, u0, nb);
+      if (on_device) CK(cudaStreamSynchronize(p->stream));
+      return SWKB_OK;
+    }
+    const double* din = u0;
+    if (!on_device) {
+      CK(cudaMemcpyAsync(p->io, u0, nb, cudaMemcpyHostToDevice, p->stream));
+      din = p->io;   // consumed by the init kernel before any output reuses io
+    }
+    double* odev = on_device ? u_out : nullptr;
+    double* ohost = on_device ? nullptr : u_out;
+    return p->precision == SWKB_FP64
+               ? run<double>(p, din, q0, n_screens, odev, ohost, snapshot_every)
+               : run<float>(p, din, q0, n_screens, odev, ohost, snapshot_every);
+  } catch (...) {
+    return fail(SWKB_ERR_INVALID_ARG, "unexpected exception");
+  }
+}
+
+swkb_status swkb_debug_screen(swkb_plan* p, int32_t q, const double* u_full, double* c,
+                              double* delta, double* r, double* a, double* u_next) {
+  try {
+    if (!p || !u_full) return fail(SWKB_ERR_INVALID_ARG, "NULL argument");
+    CK(cudaSetDevice(p->device));
+    return p->precision == SWKB_FP64 ? debug_screen<double>(p, q, u_full, c, delta, r, a, u_next)
+                                     : debug_screen<float>(p, q, u_full, c, delta, r, a, u_next);
+  } catch (...) {
+    return fail(SWKB_ERR_INVALID_ARG, "unexpected exception");
+  }
+}
+
+void swkb_plan_destroy(swkb_plan* p) { release(p); }
+
+swkb_status swkb_plan_set_timing(swkb_plan* p, int32_t on) {
+  if (!p) return fail(SWKB_ERR_INVALID_ARG, "NULL plan");
+  p->timing = on != 0;
+  p->marks.clear();
+  memset(&p->stats, 0, sizeof(p->stats));
+  return SWKB_OK;
+}
+
+swkb_status swkb_plan_get_stats(const swkb_plan* p, swkb_plan_stats* st) {
+  if (!p || !st) return fail(SWKB_ERR_INVALID_ARG, "NULL argument");
+  *st = p->stats;
+  return SWKB_OK;
+}
+
+}  // extern "C"

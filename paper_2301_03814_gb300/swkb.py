@@ -1,0 +1,297 @@
+"""Thin ctypes binding of libswkb.so (include/swkb.h).
+
+Argument marshalling only: every step of the propagation runs in the CUDA
+library.  There is no CPU fallback -- loading fails loudly when the in-tree
+library has not been built (``python -c "import __graft_entry__ as g;
+g.build()"``).  Torch is optional and used only to hand device buffers and
+streams to the library (``on_device=True`` with CUDA tensors).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, byref, c_char_p, c_double, c_int32, c_size_t, c_uint64, c_void_p
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libswkb.so")
+
+SWKB_OK = 0
+SWKB_ERR_INVALID_ARG = 1
+SWKB_ERR_OOM = 2
+SWKB_ERR_CAUSTIC = 3
+SWKB_ERR_TURNING = 4
+SWKB_ERR_RANGE = 5
+SWKB_ERR_CUDA = 6
+SWKB_ERR_TIMEOUT = 7
+SWKB_ERR_AGAIN = 8
+SWKB_NOT_READY = 9
+SWKB_ERR_CANCELLED = 10
+
+SWKB_BC_PERIODIC, SWKB_BC_NEUMANN, SWKB_BC_DIRICHLET = 0, 1, 2
+SWKB_FP64, SWKB_MIXED = 0, 1
+
+KERNEL_KINDS = ("init", "reduce", "fft", "march", "bracket", "resum", "output")
+
+EXPORTED = ("swkb_options_default", "swkb_plan_create", "swkb_plan_get_info", "swkb_propagate",
+            "swkb_debug_screen", "swkb_plan_destroy", "swkb_plan_set_timing",
+            "swkb_plan_get_stats", "swkb_server_create", "swkb_submit",
+            "swkb_poll", "swkb_cancel", "swkb_server_get_stats", "swkb_server_destroy",
+            "swkb_last_error", "swkb_status_string")
+
+
+class SwkbError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"swkb status {status}: {msg}")
+        self.status = status
+
+
+class swkb_profile(ctypes.Structure):
+    _fields_ = [("n_cols", c_int32), ("x_cols", POINTER(c_double)), ("n_p", c_int32),
+                ("z0_p", c_double), ("dz_p", c_double), ("eps", POINTER(c_double)),
+                ("eps_z", POINTER(c_double)), ("eps_zz", POINTER(c_double))]
+
+
+class swkb_domain(ctypes.Structure):
+    _fields_ = [("z_a", c_double), ("z_b", c_double), ("x0", c_double), ("bc", c_int32)]
+
+
+class swkb_options(ctypes.Structure):
+    _fields_ = [("precision", c_int32), ("theta_max", c_double), ("n_max", c_int32),
+                ("ray_stride", c_int32), ("rk4_steps", c_int32), ("absorber_frac", c_double),
+                ("autotune", c_int32), ("cuda_stream", c_void_p), ("device", c_int32)]
+
+
+class swkb_plan_info(ctypes.Structure):
+    _fields_ = [("n_fft", c_int32), ("n_max", c_int32), ("n_modes", c_int32),
+                ("n_rays", c_int32), ("n_ghost", c_int32), ("n_rays_total", c_int32),
+                ("tile_points", c_int32), ("mode_groups", c_int32), ("dz", c_double),
+                ("period", c_double), ("eps_ref", c_double), ("device_bytes", c_size_t)]
+
+
+class swkb_plan_stats(ctypes.Structure):
+    _fields_ = [("launches", c_uint64), ("screens", c_uint64),
+                ("kernel_launches", c_uint64 * len(KERNEL_KINDS)),
+                ("kernel_ms", c_double * len(KERNEL_KINDS))]
+
+
+class swkb_request(ctypes.Structure):
+    _fields_ = [("profile", POINTER(swkb_profile)), ("k", c_double),
+                ("domain", POINTER(swkb_domain)), ("n_z", c_int32), ("screen_dx", c_double),
+                ("options", POINTER(swkb_options)), ("u0", POINTER(c_double)), ("q0", c_int32),
+                ("n_screens", c_int32)]
+
+
+class swkb_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", c_uint64), ("completed", c_uint64), ("failed", c_uint64),
+                ("rejected", c_uint64), ("resident", c_int32), ("queued", c_int32),
+                ("hbm_in_use", c_size_t)]
+
+
+_lib = None
+
+
+def lib():
+    """Load the in-tree libswkb.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with paper_2301_03814_gb300.build")
+        L = ctypes.CDLL(LIB_PATH)
+        L.swkb_options_default.argtypes = [POINTER(swkb_options)]
+        L.swkb_options_default.restype = None
+        L.swkb_plan_create.argtypes = [POINTER(swkb_profile), c_double, POINTER(swkb_domain),
+                                       c_int32, c_double, POINTER(swkb_options), POINTER(c_void_p)]
+        L.swkb_plan_get_info.argtypes = [c_void_p, POINTER(swkb_plan_info)]
+        L.swkb_propagate.argtypes = [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_int32,
+                                     c_int32]
+        L.swkb_debug_screen.argtypes = [c_void_p, c_int32] + [c_void_p] * 6
+        L.swkb_plan_set_timing.argtypes = [c_void_p, c_int32]
+        L.swkb_plan_get_stats.argtypes = [c_void_p, POINTER(swkb_plan_stats)]
+        L.swkb_plan_destroy.argtypes = [c_void_p]
+        L.swkb_plan_destroy.restype = None
+        L.swkb_server_create.argtypes = [c_size_t, c_int32, c_int32, c_int32, POINTER(c_void_p)]
+        L.swkb_submit.argtypes = [c_void_p, POINTER(swkb_request), POINTER(c_uint64)]
+        L.swkb_poll.argtypes = [c_void_p, c_uint64, c_void_p, c_int32]
+        L.swkb_cancel.argtypes = [c_void_p, c_uint64]
+        L.swkb_server_get_stats.argtypes = [c_void_p, POINTER(swkb_server_stats)]
+        L.swkb_server_destroy.argtypes = [c_void_p]
+        L.swkb_server_destroy.restype = None
+        L.swkb_last_error.restype = c_char_p
+        L.swkb_status_string.restype = c_char_p
+        L.swkb_status_string.argtypes = [c_int32]
+        for name in ("swkb_plan_create", "swkb_plan_get_info", "swkb_propagate",
+                     "swkb_plan_set_timing", "swkb_plan_get_stats",
+                     "swkb_debug_screen", "swkb_server_create", "swkb_submit", "swkb_poll",
+                     "swkb_cancel", "swkb_server_get_stats"):
+            getattr(L, name).restype = c_int32
+        _lib = L
+    return _lib
+
+
+def check(status: int, allow=(SWKB_OK,)) -> int:
+    if status not in allow:
+        raise SwkbError(status, lib().swkb_last_error().decode(errors="replace"))
+    return status
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(POINTER(c_double))
+
+
+# --------------------------------------------------------------------------
+# argument marshalling
+# --------------------------------------------------------------------------
+class _Keep:
+    """Holds the numpy buffers a C struct points into."""
+
+    def __init__(self):
+        self.refs = []
+
+    def f64(self, a):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        self.refs.append(a)
+        return a
+
+
+def make_profile(profile, keep: _Keep) -> swkb_profile:
+    p = swkb_profile()
+    p.n_cols = int(profile.eps.shape[0])
+    p.n_p = int(profile.eps.shape[1])
+    p.x_cols = _dptr(keep.f64(profile.x_cols))
+    p.z0_p = float(profile.z0)
+    p.dz_p = float(profile.dz)
+    p.eps = _dptr(keep.f64(profile.eps))
+    p.eps_z = _dptr(keep.f64(profile.eps_z))
+    p.eps_zz = _dptr(keep.f64(profile.eps_zz))
+    return p
+
+
+def swkb_options_default() -> swkb_options:
+    o = swkb_options()
+    lib().swkb_options_default(byref(o))
+    return o
+
+
+def options_for(problem, precision=SWKB_FP64, stream=None, device=0) -> swkb_options:
+    o = swkb_options_default()
+    o.precision = precision
+    o.theta_max = float(problem.theta_max)
+    o.n_max = int(problem.n_max)
+    o.ray_stride = int(problem.ray_stride)
+    o.rk4_steps = int(problem.rk4_steps)
+    o.absorber_frac = float(problem.absorber_frac)
+    o.cuda_stream = stream
+    o.device = device
+    return o
+
+
+def swkb_plan_create(profile, k, domain: swkb_domain, n_z, screen_dx, options: swkb_options):
+    keep = _Keep()
+    prof = make_profile(profile, keep)
+    handle = c_void_p()
+    check(lib().swkb_plan_create(byref(prof), float(k), byref(domain), int(n_z),
+                                 float(screen_dx), byref(options), byref(handle)))
+    return handle
+
+
+def swkb_plan_get_info(plan) -> swkb_plan_info:
+    info = swkb_plan_info()
+    check(lib().swkb_plan_get_info(plan, byref(info)))
+    return info
+
+
+def swkb_propagate(plan, u0, q0, n_screens, u_out, snapshot_every=0, on_device=0):
+    """u0 / u_out: numpy complex128 arrays (host) or integer device pointers
+    (on_device=1)."""
+    if on_device:
+        return check(lib().swkb_propagate(plan, c_void_p(int(u0)), q0, n_screens,
+                                          c_void_p(int(u_out)), snapshot_every, 1))
+    return check(lib().swkb_propagate(plan, u0.ctypes.data_as(c_void_p), q0, n_screens,
+                                      u_out.ctypes.data_as(c_void_p), snapshot_every, 0))
+
+
+def swkb_plan_destroy(plan):
+    lib().swkb_plan_destroy(plan)
+
+
+def swkb_plan_set_timing(plan, on: bool):
+    check(lib().swkb_plan_set_timing(plan, 1 if on else 0))
+
+
+def swkb_plan_get_stats(plan) -> dict:
+    st = swkb_plan_stats()
+    check(lib().swkb_plan_get_stats(plan, byref(st)))
+    return {"launches": int(st.launches), "screens": int(st.screens),
+            "kernel_launches": {k: int(st.kernel_launches[i]) for i, k in enumerate(KERNEL_KINDS)},
+            "kernel_ms": {k: float(st.kernel_ms[i]) for i, k in enumerate(KERNEL_KINDS)}}
+
+
+def swkb_last_error() -> str:
+    return lib().swkb_last_error().decode(errors="replace")
+
+
+# --------------------------------------------------------------------------
+# convenience wrapper
+# --------------------------------------------------------------------------
+class Plan:
+    """A plan for one workloads.Problem (or equivalent fields)."""
+
+    def __init__(self, problem, precision=SWKB_FP64, stream=None, device=0):
+        self.problem = problem
+        dom = swkb_domain(problem.z_a, problem.z_b, problem.x0, problem.bc)
+        self.options = options_for(problem, precision, stream, device)
+        self.handle = swkb_plan_create(problem.profile, problem.k, dom, problem.n_z,
+                                       problem.dx, self.options)
+        self.info = swkb_plan_get_info(self.handle)
+        self.n_z = problem.n_z
+
+    def close(self):
+        if self.handle:
+            swkb_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def propagate(self, u0=None, q0=0, n_screens=None, snapshot_every=0):
+        """Host arrays in and out (complex128)."""
+        if u0 is None:
+            u0 = self.problem.u0
+        if n_screens is None:
+            n_screens = self.problem.n_screens
+        u0 = np.ascontiguousarray(u0, dtype=np.complex128)
+        n_out = n_screens // snapshot_every if snapshot_every else 1
+        out = np.empty(n_out * self.n_z, dtype=np.complex128)
+        swkb_propagate(self.handle, u0, q0, n_screens, out, snapshot_every, 0)
+        return out.reshape(n_out, self.n_z) if snapshot_every else out
+
+    def propagate_device(self, u0_ptr: int, out_ptr: int, q0=0, n_screens=None, snapshot_every=0):
+        if n_screens is None:
+            n_screens = self.problem.n_screens
+        return swkb_propagate(self.handle, u0_ptr, q0, n_screens, out_ptr, snapshot_every, 1)
+
+    def set_timing(self, on: bool):
+        swkb_plan_set_timing(self.handle, on)
+
+    def stats(self) -> dict:
+        return swkb_plan_get_stats(self.handle)
+
+    def debug_screen(self, q, u_full):
+        i = self.info
+        u_full = np.ascontiguousarray(u_full, dtype=np.complex128)
+        c = np.empty(i.n_modes, np.complex128)
+        shape = (i.n_modes, i.n_rays_total)
+        delta = np.empty(shape)
+        r = np.empty(shape)
+        a = np.empty(shape)
+        un = np.empty(i.n_fft, np.complex128)
+        check(lib().swkb_debug_screen(self.handle, int(q), u_full.ctypes.data_as(c_void_p),
+                                      c.ctypes.data_as(c_void_p), delta.ctypes.data_as(c_void_p),
+                                      r.ctypes.data_as(c_void_p), a.ctypes.data_as(c_void_p),
+                                      un.ctypes.data_as(c_void_p)))
+        return dict(c=c, delta=delta, r=r, a=a, u_next=un)

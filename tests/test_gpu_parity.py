@@ -1,0 +1,221 @@
+"""GPU path (libswkb.so through the C ABI) against the CPU oracle.
+
+Tolerances: FP64 path rel-L2 <= 1e-9 on the field (elementwise <= 1e-9 of the
+field's max on intermediates); mixed FP32/FP64 path rel-L2 <= 1e-4."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2301_03814_gb300 import swkb
+from paper_2301_03814_gb300 import workloads as w
+from oracle.swkb_oracle import Oracle, geometry, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-9
+MIXED_TOL = 1e-4
+
+
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    gpu()
+
+
+def _oracle_cache():
+    cache = {}
+
+    def get(name, fn):
+        if name not in cache:
+            cache[name] = fn()
+        return cache[name]
+    return get
+
+
+_cache = _oracle_cache()
+
+
+def c1_oracle():
+    pb = w.config_unit_periodic()
+    return _cache("c1", lambda: Oracle(pb).propagate(pb.u0))
+
+
+def duct_small():
+    return w.config_surface_duct_small()
+
+
+def duct_small_oracle():
+    pb = duct_small()
+    return _cache("duct", lambda: Oracle(pb).propagate(pb.u0))
+
+
+@pytest.mark.parametrize("name", ["unit-periodic", "duct-small", "homog-neumann"])
+def test_plan_geometry_matches_oracle(name):
+    pb = {"unit-periodic": w.config_unit_periodic, "duct-small": duct_small,
+          "homog-neumann": lambda: w.config_homogeneous(bc=w.BC_NEUMANN, ray_stride=2)}[name]()
+    g = geometry(pb)
+    info = swkb.Plan(pb).info
+    assert (info.n_fft, info.n_max, info.n_modes, info.n_rays, info.n_ghost,
+            info.n_rays_total) == (g.N, g.n_max, g.M, g.N_r, g.G, g.NRT)
+
+
+@pytest.mark.parametrize("q", [0, 5])
+def test_debug_screen_fp64_intermediates(q):
+    pb = w.config_unit_periodic()
+    o = Oracle(pb)
+    rng = np.random.default_rng(q)
+    u = o.extend(pb.u0) * (1 + 0.1 * rng.standard_normal(o.g.N))
+    want_u, want_c, rays = o.screen(u, q, keep_rays=True)
+    got = swkb.Plan(pb).debug_screen(q, u)
+    assert np.max(np.abs(got["c"] - want_c)) <= 1e-13 * np.max(np.abs(want_c))
+    delta = (rays["z"] - o.g.z_lo) / o.g.dz
+    # the two sides evaluate eps_zz with different rounding (the oracle's
+    # Hermite basis cancels terms of size eps / h^2): 1e-10 on the ray data
+    assert np.max(np.abs(got["delta"] - delta)) < 1e-9
+    assert np.max(np.abs(got["r"] - rays["r"])) < 1e-10
+    assert np.max(np.abs(got["a"] - rays["a"])) < 1e-10
+    assert rel_l2(got["u_next"], want_u) < FP64_TOL
+
+
+def test_debug_screen_mixed_intermediates():
+    pb = w.config_unit_periodic()
+    o = Oracle(pb)
+    u = o.extend(pb.u0)
+    want_u, want_c, rays = o.screen(u, 5, keep_rays=True)
+    got = swkb.Plan(pb, swkb.SWKB_MIXED).debug_screen(5, u)
+    assert np.max(np.abs(got["c"] - want_c)) <= 1e-6 * np.max(np.abs(want_c))
+    delta = (rays["z"] - o.g.z_lo) / o.g.dz
+    assert np.max(np.abs(got["delta"] - delta)) < 1e-4
+    # residual phase in turns: k r / (2 pi) within 1e-5 turn
+    assert np.max(np.abs(got["r"] - rays["r"])) * pb.k / (2 * math.pi) < 1e-5
+    assert np.max(np.abs(got["a"] - rays["a"])) < 1e-5
+    assert rel_l2(got["u_next"], want_u) < MIXED_TOL
+
+
+def test_unit_periodic_fp64_parity():
+    pb = w.config_unit_periodic()
+    got = swkb.Plan(pb).propagate()
+    assert rel_l2(got, c1_oracle()) < FP64_TOL
+
+
+def test_unit_periodic_mixed_parity():
+    pb = w.config_unit_periodic()
+    got = swkb.Plan(pb, swkb.SWKB_MIXED).propagate()
+    assert rel_l2(got, c1_oracle()) < MIXED_TOL
+
+
+def test_duct_small_fp64_parity():
+    pb = duct_small()
+    got = swkb.Plan(pb).propagate()
+    assert rel_l2(got, duct_small_oracle()) < FP64_TOL
+
+
+def test_duct_small_mixed_parity():
+    pb = duct_small()
+    got = swkb.Plan(pb, swkb.SWKB_MIXED).propagate()
+    assert rel_l2(got, duct_small_oracle()) < MIXED_TOL
+
+
+@pytest.mark.parametrize("bc", [w.BC_PERIODIC, w.BC_NEUMANN, w.BC_DIRICHLET])
+@pytest.mark.parametrize("prec,tol", [(swkb.SWKB_FP64, 1e-12), (swkb.SWKB_MIXED, 2e-5)])
+def test_homogeneous_vs_angular_spectrum(bc, prec, tol):
+    from refs import angular_spectrum
+    pb = w.config_homogeneous(eps0=1.1, bc=bc, ray_stride=2, rk4_steps=3)
+    got = swkb.Plan(pb, prec).propagate()
+    g = geometry(pb)
+    if bc == w.BC_PERIODIC:
+        ref = angular_spectrum(pb.u0, pb.k, g.L, pb.dx * pb.n_screens, g.n_max, 1.1)
+    else:
+        sg = 1.0 if bc == w.BC_NEUMANN else -1.0
+        n = pb.n_z
+        full = np.zeros(2 * n, complex)
+        full[n:] = pb.u0
+        full[n - np.arange(1, n)] = sg * pb.u0[1:]
+        ref = angular_spectrum(full, pb.k, g.L, pb.dx * pb.n_screens, g.n_max, 1.1)[n:]
+    assert rel_l2(got, ref) < tol
+
+
+def test_snapshots_and_resume_match_one_call():
+    pb = w.config_unit_periodic()
+    plan = swkb.Plan(pb)
+    snaps = plan.propagate(snapshot_every=2)
+    assert snaps.shape == (5, pb.n_z)
+    whole = plan.propagate()
+    assert np.array_equal(snaps[-1], whole)
+    half = plan.propagate(n_screens=4)
+    rest = plan.propagate(u0=half, q0=4, n_screens=6)
+    assert np.array_equal(rest, whole)
+
+
+def test_device_pointers_and_stream():
+    torch = gpu()
+    pb = w.config_unit_periodic(n_screens=3)
+    s = torch.cuda.Stream()
+    plan = swkb.Plan(pb, swkb.SWKB_MIXED, stream=s.cuda_stream)
+    u0 = torch.from_numpy(pb.u0).cuda()
+    out = torch.empty_like(u0)
+    plan.propagate_device(u0.data_ptr(), out.data_ptr())
+    host = plan.propagate()
+    assert np.array_equal(out.cpu().numpy(), host)
+
+
+def test_caustic_reported():
+    pb = w.config_gaussian_medium(a=0.05, b=0.01, dx=100.0, n_screens=1)
+    pr = pb.profile   # a taller table, so that the plan accepts the long screen
+    pb = pb.with_(profile=w._table([0.0], -160.0, pr.dz, int(384 / pr.dz) + 1,
+                                   [w.f_gaussian(0.05, 0.01, zc=32.0)]))
+    with pytest.raises(swkb.SwkbError) as e:
+        swkb.Plan(pb).propagate()
+    assert e.value.status == swkb.SWKB_ERR_CAUSTIC
+
+
+def test_turning_reported():
+    k = 2 * math.pi
+    prof = w._table([0.0, 20.0], -200.0, 0.125, 3201, [w.f_const(1.0), w.f_const(0.5)])
+    z = 64.0 / 256 * np.arange(256)
+    pb = w.Problem("turn", k, 0.0, 64.0, 256, w.BC_PERIODIC, 0.0, 20.0, 1, prof,
+                   w.gaussian_beam(z, k, 32, 3, 0.0), math.radians(60.0), 1, 8)
+    for prec in (swkb.SWKB_FP64, swkb.SWKB_MIXED):
+        with pytest.raises(swkb.SwkbError) as e:
+            swkb.Plan(pb, prec).propagate()
+        assert e.value.status == swkb.SWKB_ERR_TURNING
+
+
+def test_short_table_rejected_at_plan_creation():
+    k = 2 * math.pi
+    prof = w._table([0.0], -2.0, 0.125, 540, [w.f_const(1.0)])
+    z = 64.0 / 256 * np.arange(256)
+    pb = w.Problem("short", k, 0.0, 64.0, 256, w.BC_PERIODIC, 0.0, 20.0, 1, prof,
+                   w.gaussian_beam(z, k, 32, 3, 0.0), math.radians(30.0), 1, 8)
+    with pytest.raises(swkb.SwkbError) as e:
+        swkb.Plan(pb)
+    assert e.value.status == swkb.SWKB_ERR_INVALID_ARG
+
+
+def test_full_size_duct_one_screen_fp64_vs_oracle():
+    """Bench workload at full size (N_z = 16384, 977 modes): one screen from
+    the antenna field through the same plan shape the benchmark times; the
+    whole field is compared (the oracle finishes one screen in seconds)."""
+    pb = w.config_surface_duct(n_screens=200)
+    o = Oracle(pb)
+    u = o.extend(pb.u0)
+    want = o.screen(u, 7)
+    got = swkb.Plan(pb).debug_screen(7, u)["u_next"]
+    assert rel_l2(got, want) < FP64_TOL
+
+
+def test_full_size_duct_mixed_vs_fp64_200_screens():
+    """Whole 10 km / 200-screen bench workload: mixed path within 1e-4 of the
+    FP64 path (the FP64 path is tied to the oracle above)."""
+    pb = w.config_surface_duct()
+    a = swkb.Plan(pb).propagate()
+    b = swkb.Plan(pb, swkb.SWKB_MIXED).propagate()
+    assert np.all(np.isfinite(a)) and np.linalg.norm(a) > 0.1 * np.linalg.norm(pb.u0)
+    assert rel_l2(b, a) < MIXED_TOL
