@@ -198,6 +198,34 @@ typedef struct {
 swkb_status swkb_plan_set_timing(swkb_plan* plan, int32_t on);
 swkb_status swkb_plan_get_stats(const swkb_plan* plan, swkb_plan_stats* stats);
 
+/*
+ * Step (a) -- the pruned DFT of one screen field, c_n = w_n / N for
+ * |n| <= n_max (FP64) -- without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc, such as host frameworks that own and pre-partition all device
+ * memory and forbid other allocators, or latency-critical loops in which an
+ * allocation would synchronise the device and stall other work.
+ *
+ * u: device pointer, n_fft complex128 values of the screen field on its whole
+ * period; c: device pointer, 2 n_max + 1 complex128 outputs (n = -n_max ..
+ * n_max).  Both stay owned by the caller.  n_fft must be a power of two in
+ * [64, 65536] and 1 <= n_max <= n_fft / 2 - 1; anything larger is rejected
+ * with SWKB_ERR_INVALID_ARG, as are host pointers.  The call is asynchronous
+ * on cuda_stream (NULL = the default stream).
+ *
+ * The working storage is a fixed set of file-scope device arrays (about
+ * 2.5 MB) that every GPU loading this library holds until the process exits.
+ * The first call on a device performs a one-time set-up on that device (it
+ * resolves the arrays' device addresses, initialises one of them and
+ * synchronises the device); make that first call before any stream capture.
+ * All calls on a device share the arrays and leave the last call's contents
+ * in them (each call rewrites everything it reads, so nothing needs
+ * clearing); calls that overlap on the GPU -- e.g. on two streams at once --
+ * race on the arrays and must be serialised by the caller.
+ */
+swkb_status swkb_modes_noalloc(const double* u, int32_t n_fft, int32_t n_max, double* c,
+                               void* cuda_stream);
+
 /* ---------------------------------------------------------------------------
  * Serving: a continuous-batching request loop.  Requests (each a whole
  * propagation job) are admitted while their device footprint fits the HBM

@@ -111,5 +111,9 @@ template <typename T> size_t resum_smem_bytes(int wcap, int warps_per_cta);
 // Raise the dynamic shared-memory limits of the FFT and resummation kernels
 // on the current device (call once per device before launching).
 template <typename T> cudaError_t prepare_kernels(int resum_smem);
+// Message returned by swkb_last_error() on this thread.
+void set_last_error(const char* msg);
+// Raise only the FFT kernel's shared-memory limit on the current device.
+template <typename T> cudaError_t prepare_fft_kernels();
 
 }  // namespace swkb

@@ -573,6 +573,12 @@ cudaError_t prepare_kernels(int resum_smem) {
 }
 
 template <typename T>
+cudaError_t prepare_fft_kernels() {
+  return cudaFuncSetAttribute(k_fft2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)(2 * 4096 * sizeof(typename C2<T>::type)));
+}
+
+template <typename T>
 cudaError_t launch_output(const typename C2<T>::type* u, int offset, int n, double* out,
                           cudaStream_t s) {
   k_output<T><<<(n + 255) / 256, 256, 0, s>>>(u, offset, n, out);
@@ -588,7 +594,8 @@ cudaError_t launch_output(const typename C2<T>::type* u, int offset, int n, doub
   template cudaError_t launch_resum<T>(const ResumArgs<T>&, int, cudaStream_t);                 \
   template cudaError_t launch_output<T>(const C2<T>::type*, int, int, double*, cudaStream_t);   \
   template size_t resum_smem_bytes<T>(int, int);                                                \
-  template cudaError_t prepare_kernels<T>(int);
+  template cudaError_t prepare_kernels<T>(int);                                                 \
+  template cudaError_t prepare_fft_kernels<T>();
 
 SWKB_INSTANTIATE(float)
 SWKB_INSTANTIATE(double)

@@ -58,6 +58,8 @@ int ilog2(long long v) {
 
 }  // namespace
 
+void swkb::set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+
 struct swkb_plan {
   // problem
   int precision = SWKB_FP64;

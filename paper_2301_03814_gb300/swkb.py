@@ -38,7 +38,7 @@ EXPORTED = ("swkb_options_default", "swkb_plan_create", "swkb_plan_get_info", "s
             "swkb_debug_screen", "swkb_plan_destroy", "swkb_plan_set_timing",
             "swkb_plan_get_stats", "swkb_server_create", "swkb_submit",
             "swkb_poll", "swkb_cancel", "swkb_server_get_stats", "swkb_server_destroy",
-            "swkb_last_error", "swkb_status_string")
+            "swkb_last_error", "swkb_status_string", "swkb_modes_noalloc")
 
 
 class SwkbError(RuntimeError):
@@ -118,6 +118,8 @@ def lib():
         L.swkb_server_get_stats.argtypes = [c_void_p, POINTER(swkb_server_stats)]
         L.swkb_server_destroy.argtypes = [c_void_p]
         L.swkb_server_destroy.restype = None
+        L.swkb_modes_noalloc.argtypes = [c_void_p, c_int32, c_int32, c_void_p, c_void_p]
+        L.swkb_modes_noalloc.restype = c_int32
         L.swkb_last_error.restype = c_char_p
         L.swkb_status_string.restype = c_char_p
         L.swkb_status_string.argtypes = [c_int32]
@@ -226,6 +228,12 @@ def swkb_plan_get_stats(plan) -> dict:
     return {"launches": int(st.launches), "screens": int(st.screens),
             "kernel_launches": {k: int(st.kernel_launches[i]) for i, k in enumerate(KERNEL_KINDS)},
             "kernel_ms": {k: float(st.kernel_ms[i]) for i, k in enumerate(KERNEL_KINDS)}}
+
+
+def swkb_modes_noalloc(u_ptr: int, n_fft: int, n_max: int, c_ptr: int, stream=None) -> int:
+    """Pruned DFT of a device field (device pointers) with no device allocation."""
+    return lib().swkb_modes_noalloc(c_void_p(int(u_ptr)), int(n_fft), int(n_max),
+                                    c_void_p(int(c_ptr)), stream)
 
 
 def swkb_last_error() -> str:
