@@ -304,9 +304,9 @@ def run_ours(args, world, rank, local):
     info = plan.info
     peak_fp32 = 152 * 128 * 2 * 2.07e9 / 1e12
     if dom == "march":
-        work = march_flops_per_ray(pb) * info.n_modes * info.n_rays_total
+        work = march_flops_per_ray(pb) * info.march_modes * info.n_rays_total
     elif dom == "resum":
-        work = resum_flops_per_term() * info.n_modes * info.n_fft
+        work = resum_flops_per_term() * info.n_modes * info.resum_points
     else:
         work = None
     roofline = None

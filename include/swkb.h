@@ -118,6 +118,10 @@ typedef struct {
   int32_t n_rays_total;   /* n_rays + 2 n_ghost (per mode)                    */
   int32_t tile_points;    /* grid points per resummation tile                 */
   int32_t mode_groups;    /* mode groups of the resummation                   */
+  int32_t march_modes;    /* modes whose rays are marched (grounded domains:
+                             n >= 0 only -- mode -n is the mirror image)      */
+  int32_t resum_points;   /* grid points summed per screen (grounded domains:
+                             the physical half plus one tile)                 */
   double dz, period;      /* grid spacing, period length                      */
   double eps_ref;         /* reference permittivity of the phase carry        */
   size_t device_bytes;    /* device memory held by the plan                   */
@@ -158,12 +162,17 @@ swkb_status swkb_propagate(swkb_plan* plan, const double* u0, int32_t q0, int32_
 /*
  * One screen with every intermediate exposed, for testing (host pointers;
  * any output may be NULL).  u_full: N complex128 values on the whole period
- * (z_lo + m dz; z_lo = 2 z_a - z_b when grounded).  Outputs: c [n_modes]
+ * (z_lo + m dz; z_lo = 2 z_a - z_b when grounded; a grounded plan expects
+ * the even (Neumann) or odd (Dirichlet) field every grounded screen carries,
+ * and forms c_{-n} = +-c_n from it).  Outputs: c [n_modes]
  * complex128 mode coefficients w_n / N (step a); delta, r, a [n_modes]
  * [n_rays_total] float64 ray landing (grid units from z_lo), residual phase
  * r = psi - kappa_n (z - z_lo) and amplitude factor sqrt(P0 / (P1 Z_s))
  * (step b); u_next N complex128: the modal sum times the absorber, before the
- * reflection step (steps c, d).
+ * reflection step (steps c, d).  Grounded plans march modes n >= 0 and sum
+ * the physical half only: their rays of mode -n are returned as the mirror
+ * images of mode n's (ray 0, which has no mirror partner, as NaN) and the
+ * other half of u_next as the reflection of the physical half.
  */
 swkb_status swkb_debug_screen(swkb_plan* plan, int32_t q, const double* u_full, double* c,
                               double* delta, double* r, double* a, double* u_next);

@@ -34,7 +34,10 @@ def sources():
 def build(verbose: bool = False, extra=()) -> str:
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
-    common = ["-O3", "-std=c++17", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC",
+    # FP32 denormals never occur on this path (deviation variables are >= 1e-12),
+    # and every FP32 quotient that must be exact is a power of two done by scalbn
+    common = ["-O3", "-std=c++17", "-lineinfo", *ARCH, "-ftz=true", "-prec-div=false",
+              "-prec-sqrt=false", "-Xcompiler", "-fPIC",
               "-I", os.path.join(ROOT, "include"), "-I", CSRC, *extra]
 
     def compile_one(src):

@@ -48,19 +48,23 @@ struct MarchArgs {
   const T* kappa;   // [M] kappa_n
   const T* pbar;    // [M] sqrt(eps_ref - kappa_n^2)
   const T* pbar2;   // [M] eps_ref - kappa_n^2
-  int M, NRT, G, R, Nt;
+  int Mr;           // marched modes (row length of the outputs)
+  int mode_off;     // marched mode r is mode index r + mode_off (n = r + mode_off - n_max)
+  int NRT, G, R, Nt;
   T z_lo, dz, inv_dz, h, k_over_2pi;
-  T* out_d;         // [NRT][M] landing offset from the launch grid point, grid units
-  T* out_ph;        // [NRT][M] residual phase k (r - x P_bar) / (2 pi), turns
-  T* out_a;         // [NRT][M] amplitude factor sqrt(P0 / (P1 Z_s))
+  T* out_d;         // [NRT][Mr] landing offset from the launch grid point, grid units
+  T* out_ph;        // [NRT][Mr] residual phase k (r - x P_bar) / (2 pi), turns
+  T* out_a;         // [NRT][Mr] amplitude factor sqrt(P0 / (P1 Z_s))
   unsigned* status;
 };
 
 template <typename T>
 struct BracketArgs {
-  const T* d;       // [NRT][M]
-  int M, NRT, G, R, N, TM, n_tiles;
-  int* jlo;         // [n_tiles + 1][M] bracket ray of each tile start
+  const T* d;       // [NRT][Mr]
+  int Mr, NRT, G, R, N, TM, n_tiles;
+  int* jlo;         // [n_tiles + 1][Mr] bracket ray of each tile start
+  int sym;          // grounded domain: also the mirrored family of each mode
+  int* jlo_neg;     // [n_tiles + 1][Mr] brackets of the mirror image (mode -n)
   unsigned* status;
 };
 
@@ -70,9 +74,13 @@ struct ResumArgs {
   const T* ph;
   const T* a;
   const int* jlo;
+  const int* jlo_neg;
   const typename C2<T>::type* c;   // [M] mode coefficients, range phase folded in
-  int M, NRT, G, R, N, TM, PW, n_tiles, n_groups, modes_per_group, n_max, wcap;
-  typename C2<T>::type* part;      // [n_groups][N]
+  int M, Mr, NRT, G, R, N, TM, PW, n_tiles, n_groups, modes_per_group, n_max, wcap;
+  int sym;          // grounded: modes n < 0 are mirror images of -n; only the
+                    // tiles of the physical half and tile 0 are summed
+  int n_tiles_run;  // tiles summed per mode group
+  typename C2<T>::type* part;      // [n_groups][N], one partial sum per mode group
   unsigned* status;
 };
 
@@ -82,6 +90,7 @@ struct ReduceArgs {
   int n_part, N;
   const T* W;                        // [N] absorber or nullptr
   int mirror;                        // 0 none, +1 even, -1 odd
+  int sym;                           // partials cover only m >= N/2 and m = 0
   typename C2<T>::type* u;           // [N]
 };
 
@@ -91,6 +100,7 @@ struct FftArgs {
   const typename C2<T>::type* tw;    // [N] exp(-2 pi i k / N)
   typename C2<T>::type* Y;           // [N1][N2]
   int N, N1, N2, log2N2, n_max;
+  int mirror;                        // 0, or +-1: the field is even / odd
   T inv_N;
   const typename C2<T>::type* ephi;  // [M] exp(i Phi_n)
   typename C2<T>::type* c;           // [M]
@@ -101,14 +111,14 @@ template <typename T> cudaError_t launch_init(const double* u0, int n_z, int N, 
                                               typename C2<T>::type* u, cudaStream_t s);
 template <typename T> cudaError_t launch_reduce(const ReduceArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_fft(const FftArgs<T>& a, cudaStream_t s);
-template <typename T> cudaError_t launch_march(const MarchArgs<T>& a, cudaStream_t s);
-template <typename T> cudaError_t launch_bracket(const BracketArgs<T>& a, cudaStream_t s);
-template <typename T> cudaError_t launch_resum(const ResumArgs<T>& a, int warps_per_cta,
+template <typename T> cudaError_t launch_march(const MarchArgs<T>& a, bool multi_column,
                                                cudaStream_t s);
+template <typename T> cudaError_t launch_bracket(const BracketArgs<T>& a, cudaStream_t s);
+template <typename T> cudaError_t launch_resum(const ResumArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_output(const typename C2<T>::type* u, int offset, int n,
                                                 double* out, cudaStream_t s);
-template <typename T> size_t resum_smem_bytes(int wcap, int warps_per_cta);
-// Raise the dynamic shared-memory limits of the FFT and resummation kernels
+template <typename T> size_t resum_smem_bytes(int wcap, int tile_points);
+// Raise the dynamic shared-memory limit of the resummation kernels
 // on the current device (call once per device before launching).
 template <typename T> cudaError_t prepare_kernels(int resum_smem);
 // Message returned by swkb_last_error() on this thread.

@@ -39,6 +39,22 @@ namespace swkb {
 __device__ __forceinline__ void sincospi_t(float x, float* s, float* c) { sincospif(x, s, c); }
 __device__ __forceinline__ void sincospi_t(double x, double* s, double* c) { sincospi(x, s, c); }
 
+// sin / cos of 2 pi t for |t| <= 1/2: the FP32 path uses the special-function
+// unit (absolute error ~2^-21 on [-pi, pi]); the FP64 path stays exact.
+__device__ __forceinline__ void sincos_turns(float t, float* s, float* c) {
+  __sincosf(6.28318530717958647692f * t, s, c);
+}
+__device__ __forceinline__ void sincos_turns(double t, double* s, double* c) {
+  sincospi(2.0 * t, s, c);
+}
+
+// 1/sqrt: FP32 via the special-function unit (2 ulp), FP64 correctly-rounded
+// to 1 ulp.  Small-quotient division: FP32 fast (2 ulp), FP64 IEEE.
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
+__device__ __forceinline__ float fdiv_t(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fdiv_t(double a, double b) { return a / b; }
+
 template <typename T>
 __device__ __forceinline__ void load6(const T* p, T& a0, T& a1, T& a2, T& a3, T& a4, T& a5);
 
@@ -66,28 +82,29 @@ template <typename T>
 __device__ __forceinline__ void col_eval(const Medium<T>& m, int c, T zz, T& e, T& ez, T& ezz,
                                          unsigned& st) {
   const T u = (zz - m.z0) * m.inv_h;
-  int i;
-  T t;
-  if (!(u >= T(0))) {                       // below the table (or NaN)
-    st |= ST_RANGE; i = 0; t = T(0);
-  } else {
-    const T fi = floor(u);
-    if (fi >= T(m.n_int)) {
-      if (!(fi == T(m.n_int) && u == fi)) st |= ST_RANGE;
-      i = m.n_int - 1; t = T(1);
-    } else {
-      i = (int)fi; t = u - fi;
-    }
-  }
+  // outside [0, n_int] (or NaN): flag and clamp to the nearest end interval
+  if (!(u >= T(0) && u <= T(m.n_int))) st |= ST_RANGE;
+  const T fi = fmin(fmax(floor(u), T(0)), T(m.n_int - 1));
+  const T t = fmin(fmax(u - fi, T(0)), T(1));
+  const int i = (int)fi;
   T a0, a1, a2, a3, a4, a5;
   load6<T>(m.coef + (long long)c * m.col_stride + (long long)i * 8, a0, a1, a2, a3, a4, a5);
-  e = a0 + t * (a1 + t * (a2 + t * (a3 + t * (a4 + t * a5))));
-  ez = (a1 + t * (T(2) * a2 + t * (T(3) * a3 + t * (T(4) * a4 + t * (T(5) * a5))))) * m.inv_h;
-  ezz = (T(2) * a2 + t * (T(6) * a3 + t * (T(12) * a4 + t * (T(20) * a5)))) * m.inv_h2;
+  // Horner with derivatives (synthetic division): p, p', p''/2 at t
+  T b = a5 * t + a4;                                     // coefficient 4
+  T d2 = a5;                                             // coefficient 3
+  T d1 = a5 * t + b;
+  b = b * t + a3;
+  d2 = d2 * t + d1; d1 = d1 * t + b; b = b * t + a2;     // coefficient 2
+  d2 = d2 * t + d1; d1 = d1 * t + b; b = b * t + a1;     // coefficient 1
+  d2 = d2 * t + d1; d1 = d1 * t + b; b = b * t + a0;     // coefficient 0
+  e = b;
+  ez = d1 * m.inv_h;
+  ezz = d2 * m.inv_h2;   // inv_h2 = 2 / h^2
 }
 
-// eps - eps_ref, eps_z, eps_zz at RK4 stage l and height z.
-template <typename T>
+// eps - eps_ref, eps_z, eps_zz at RK4 stage l and height z.  MULTI: the
+// profile has several range columns (else column 0 everywhere).
+template <typename T, bool MULTI>
 __device__ __forceinline__ void medium_eval(const MarchArgs<T>& p, int l, T z, T& e, T& ez,
                                             T& ezz, unsigned& st) {
   T zz = z, sg = T(1);
@@ -96,19 +113,23 @@ __device__ __forceinline__ void medium_eval(const MarchArgs<T>& p, int l, T z, T
     sg = d < T(0) ? T(-1) : T(1);
     zz = p.med.z_mirror + fabs(d);
   }
-  const int c = __ldg(p.st.c + l);
-  const T th = __ldg(p.st.th + l);
-  if (th == T(0)) {
-    col_eval(p.med, c, zz, e, ez, ezz, st);
-  } else if (th == T(1)) {
-    col_eval(p.med, c + 1, zz, e, ez, ezz, st);
+  if (!MULTI) {
+    col_eval(p.med, 0, zz, e, ez, ezz, st);
   } else {
-    T e0, ez0, ezz0, e1, ez1, ezz1;
-    col_eval(p.med, c, zz, e0, ez0, ezz0, st);
-    col_eval(p.med, c + 1, zz, e1, ez1, ezz1, st);
-    e = (T(1) - th) * e0 + th * e1;
-    ez = (T(1) - th) * ez0 + th * ez1;
-    ezz = (T(1) - th) * ezz0 + th * ezz1;
+    const int c = __ldg(p.st.c + l);
+    const T th = __ldg(p.st.th + l);
+    if (th == T(0)) {
+      col_eval(p.med, c, zz, e, ez, ezz, st);
+    } else if (th == T(1)) {
+      col_eval(p.med, c + 1, zz, e, ez, ezz, st);
+    } else {
+      T e0, ez0, ezz0, e1, ez1, ezz1;
+      col_eval(p.med, c, zz, e0, ez0, ezz0, st);
+      col_eval(p.med, c + 1, zz, e1, ez1, ezz1, st);
+      e = (T(1) - th) * e0 + th * e1;
+      ez = (T(1) - th) * ez0 + th * ez1;
+      ezz = (T(1) - th) * ezz0 + th * ezz1;
+    }
   }
   ez *= sg;
 }
@@ -127,23 +148,23 @@ struct Ray {
 //   Q_s' = (eps_zz Z_s - eps_z P_s/P)/(2P)
 // in deviation form: with e = eps - eps_ref and D = e - dQ (2 kappa + dQ),
 // P^2 = P_bar^2 + D and r' - P_bar = (e - kappa dQ - P_bar D/(P_bar + P))/P.
-template <typename T>
+template <typename T, bool MULTI>
 __device__ __forceinline__ Ray<T> rhs(const MarchArgs<T>& p, int l, T s, T kap, T pb, T pb2,
                                       const Ray<T>& y, unsigned& st) {
   T e, ez, ezz;
-  medium_eval(p, l, s + y.dz, e, ez, ezz, st);
+  medium_eval<T, MULTI>(p, l, s + y.dz, e, ez, ezz, st);
   const T Q = kap + y.dQ;
   const T D = e - y.dQ * (T(2) * kap + y.dQ);
   T P2 = pb2 + D;
   if (!(P2 > T(0))) { st |= ST_TURNING; P2 = pb2; }
   if (!(y.Zs > T(0))) st |= ST_CAUSTIC;
-  const T P = sqrt(P2);
-  const T iP = T(1) / P;
+  const T iP = rsqrt_t(P2);
+  const T P = P2 * iP;
   Ray<T> d;
   d.dz = Q * iP;
   d.dQ = T(0.5) * ez * iP;
-  d.rh = (e - kap * y.dQ - pb * D / (pb + P)) * iP;
-  const T PsiP = (ez * y.Zs - T(2) * Q * y.Qs) * (T(0.5) * iP) * iP;   // P_s / P
+  d.rh = (e - kap * y.dQ - pb * fdiv_t(D, pb + P)) * iP;
+  const T PsiP = (ez * y.Zs - T(2) * Q * y.Qs) * (T(0.5) * iP * iP);   // P_s / P
   d.Zs = (y.Qs - Q * PsiP) * iP;
   d.Qs = T(0.5) * (ezz * y.Zs - ez * PsiP) * iP;
   return d;
@@ -157,26 +178,27 @@ __device__ __forceinline__ Ray<T> axpy(const Ray<T>& y, T a, const Ray<T>& k) {
 
 // Block (32, 8): lanes are 32 consecutive modes at one launch height, so a
 // warp's table reads stay within a few z-intervals; warps are 8 rays.
-template <typename T>
+template <typename T, bool MULTI>
 __global__ void __launch_bounds__(256) k_march(const MarchArgs<T> p) {
-  const int i = blockIdx.x * 32 + threadIdx.x;
+  const int r = blockIdx.x * 32 + threadIdx.x;       // marched mode (output column)
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= p.M || j >= p.NRT) return;
+  if (r >= p.Mr || j >= p.NRT) return;
   unsigned st = 0;
+  const int i = r + p.mode_off;
   const T kap = p.kappa[i], pb = p.pbar[i], pb2 = p.pbar2[i];
   const T s = p.z_lo + T((j - p.G) * p.R) * p.dz;
   T e, ez, ezz;
-  medium_eval(p, 0, s, e, ez, ezz, st);
+  medium_eval<T, MULTI>(p, 0, s, e, ez, ezz, st);
   T P0sq = pb2 + e;
   if (!(P0sq > T(0))) { st |= ST_TURNING; P0sq = pb2; }
   const T P0 = sqrt(P0sq);
   Ray<T> y{T(0), T(0), T(0), T(1), T(0)};
   const T h = p.h, hh = T(0.5) * p.h, h6 = p.h / T(6);
   for (int n = 0; n < p.Nt; ++n) {
-    const Ray<T> k1 = rhs(p, 2 * n, s, kap, pb, pb2, y, st);
-    const Ray<T> k2 = rhs(p, 2 * n + 1, s, kap, pb, pb2, axpy(y, hh, k1), st);
-    const Ray<T> k3 = rhs(p, 2 * n + 1, s, kap, pb, pb2, axpy(y, hh, k2), st);
-    const Ray<T> k4 = rhs(p, 2 * n + 2, s, kap, pb, pb2, axpy(y, h, k3), st);
+    const Ray<T> k1 = rhs<T, MULTI>(p, 2 * n, s, kap, pb, pb2, y, st);
+    const Ray<T> k2 = rhs<T, MULTI>(p, 2 * n + 1, s, kap, pb, pb2, axpy(y, hh, k1), st);
+    const Ray<T> k3 = rhs<T, MULTI>(p, 2 * n + 1, s, kap, pb, pb2, axpy(y, hh, k2), st);
+    const Ray<T> k4 = rhs<T, MULTI>(p, 2 * n + 2, s, kap, pb, pb2, axpy(y, h, k3), st);
     y.dz += h6 * (k1.dz + T(2) * k2.dz + T(2) * k3.dz + k4.dz);
     y.dQ += h6 * (k1.dQ + T(2) * k2.dQ + T(2) * k3.dQ + k4.dQ);
     y.rh += h6 * (k1.rh + T(2) * k2.rh + T(2) * k3.rh + k4.rh);
@@ -184,14 +206,14 @@ __global__ void __launch_bounds__(256) k_march(const MarchArgs<T> p) {
     y.Qs += h6 * (k1.Qs + T(2) * k2.Qs + T(2) * k3.Qs + k4.Qs);
   }
   if (!(y.Zs > T(0))) st |= ST_CAUSTIC;
-  medium_eval(p, 2 * p.Nt, s + y.dz, e, ez, ezz, st);
+  medium_eval<T, MULTI>(p, 2 * p.Nt, s + y.dz, e, ez, ezz, st);
   T P1sq = pb2 + e - y.dQ * (T(2) * kap + y.dQ);
   if (!(P1sq > T(0))) { st |= ST_TURNING; P1sq = pb2; }
   const T Zs = y.Zs > T(0) ? y.Zs : T(1);
-  const long long o = (long long)j * p.M + i;
+  const long long o = (long long)j * p.Mr + r;
   p.out_d[o] = y.dz * p.inv_dz;
   p.out_ph[o] = y.rh * p.k_over_2pi;
-  p.out_a[o] = sqrt(P0 / (sqrt(P1sq) * Zs));
+  p.out_a[o] = sqrt(P0 * rsqrt_t(P1sq) / Zs);
   if (st) atomicOr(p.status, st);
 }
 
@@ -204,158 +226,269 @@ template <typename T>
 __global__ void k_bracket(const BracketArgs<T> p) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
-  if (i >= p.M || j >= p.NRT - 1) return;
-  const T d0 = p.d[(long long)j * p.M + i];
-  const T d1 = p.d[(long long)(j + 1) * p.M + i];
-  const long long b0 = (long long)(j - p.G) * p.R;
-  const long long b1 = b0 + p.R;
+  if (i >= p.Mr || j >= p.NRT - 1) return;
+  const T d0 = p.d[(long long)j * p.Mr + i];
+  const T d1 = p.d[(long long)(j + 1) * p.Mr + i];
+  const int b0 = (j - p.G) * p.R;   // |b0| <= N + G R < 2^31
+  const int b1 = b0 + p.R;
   unsigned st = 0;
-  if (!(T(p.R) + d1 - d0 > T(0))) st |= ST_CAUSTIC;                  // g_{j+1} > g_j
-  if (j == 1 && !(d0 <= T(-b0))) st |= ST_COVER;                      // g_1 <= 0
-  if (j + 1 == p.NRT - 2 && !(d1 > T((long long)p.N - b1))) st |= ST_COVER;  // g_{NRT-2} > N
+  if (!(T(p.R) + d1 - d0 > T(0))) st |= ST_CAUSTIC;              // g_{j+1} > g_j
+  if (j == 1 && !(d0 <= T(-b0))) st |= ST_COVER;                  // g_1 <= 0
+  if (j + 1 == p.NRT - 2 && !(d1 > T(p.N - b1))) st |= ST_COVER;  // g_{NRT-2} > N
+  if (p.sym) {   // the mirror family g'_{j'} = N - g_{NRT-j'} must cover too
+    if (j == 2 && !(d0 < T(-b0))) st |= ST_COVER;                 // g_2 < 0
+    if (j + 1 == p.NRT - 1 && !(d1 >= T(p.N - b1))) st |= ST_COVER;  // g_{NRT-1} >= N
+  }
   if (st) {
     atomicOr(p.status, st);
     return;
   }
-  const long long TM = p.TM;
-  long long t0 = (long long)ceil(((double)b0 + (double)d0) / (double)TM);
-  long long t1 = (long long)ceil(((double)b1 + (double)d1) / (double)TM) - 1;
-  t0 = t0 < -1 ? -1 : (t0 > p.n_tiles + 1 ? p.n_tiles + 1 : t0);
-  t1 = t1 < -1 ? -1 : (t1 > p.n_tiles + 1 ? p.n_tiles + 1 : t1);
-  // exact fix-ups: t0 = min t with t TM >= g_j, t1 = max t with t TM < g_{j+1}
-  for (int k = 0; k < 4 && d0 <= T((t0 - 1) * TM - b0); ++k) --t0;
-  for (int k = 0; k < 4 && !(d0 <= T(t0 * TM - b0)); ++k) ++t0;
-  for (int k = 0; k < 4 && !(T(t1 * TM - b1) < d1); ++k) --t1;
-  for (int k = 0; k < 4 && T((t1 + 1) * TM - b1) < d1; ++k) ++t1;
-  if (t0 < 0) t0 = 0;
-  if (t1 > p.n_tiles) t1 = p.n_tiles;
-  for (long long t = t0; t <= t1; ++t) p.jlo[t * p.M + i] = j;
+  const int TM = p.TM;
+  const float inv_tm = 1.0f / (float)TM;   // exact (TM is a power of two)
+  {
+    // tile starts t TM in [g_j, g_{j+1})
+    int t0 = (int)ceilf(((float)b0 + (float)d0) * inv_tm);
+    int t1 = (int)ceilf(((float)b1 + (float)d1) * inv_tm) - 1;
+    t0 = min(max(t0, -1), p.n_tiles + 1);
+    t1 = min(max(t1, -1), p.n_tiles + 1);
+    for (int k = 0; k < 4 && d0 <= T((t0 - 1) * TM - b0); ++k) --t0;
+    for (int k = 0; k < 4 && !(d0 <= T(t0 * TM - b0)); ++k) ++t0;
+    for (int k = 0; k < 4 && !(T(t1 * TM - b1) < d1); ++k) --t1;
+    for (int k = 0; k < 4 && T((t1 + 1) * TM - b1) < d1; ++k) ++t1;
+    t0 = max(t0, 0);
+    t1 = min(t1, p.n_tiles);
+    for (int t = t0; t <= t1; ++t) p.jlo[(long long)t * p.Mr + i] = j;
+  }
+  if (p.sym) {
+    // mirror family: ray j' = NRT - 1 - j ... lands at N - g.  Its bracket of
+    // tile start t TM is j' when g_j < N - t TM <= g_{j+1}.
+    int t0 = (int)ceilf(((float)p.N - (float)b1 - (float)d1) * inv_tm);
+    int t1 = (int)ceilf(((float)p.N - (float)b0 - (float)d0) * inv_tm) - 1;
+    t0 = min(max(t0, -1), p.n_tiles + 1);
+    t1 = min(max(t1, -1), p.n_tiles + 1);
+    // t0 = min t with N - t TM <= g_{j+1};  t1 = max t with g_j < N - t TM
+    for (int k = 0; k < 4 && T(p.N - (t0 - 1) * TM - b1) <= d1; ++k) --t0;
+    for (int k = 0; k < 4 && !(T(p.N - t0 * TM - b1) <= d1); ++k) ++t0;
+    for (int k = 0; k < 4 && !(d0 < T(p.N - t1 * TM - b0)); ++k) --t1;
+    for (int k = 0; k < 4 && d0 < T(p.N - (t1 + 1) * TM - b0); ++k) ++t1;
+    t0 = max(t0, 0);
+    t1 = min(t1, p.n_tiles);
+    for (int t = t0; t <= t1; ++t) p.jlo_neg[(long long)t * p.Mr + i] = p.NRT - 1 - j;
+  }
 }
 
 // ----------------------------------------------------------------------------
 // (c) + (d) interpolation fused with the modal sum
 // ----------------------------------------------------------------------------
-// One warp owns TM = 32 PW consecutive grid points (PW per lane) of one tile
-// and sums the modes of one mode group into registers.  For every mode the
-// rays landing on the tile (brackets jlo[t] .. jlo[t+1], stencil -1 / +2) are
-// staged in shared memory (a global-memory view is used if they do not fit);
-// each lane walks its bracket, builds the Newton form of the 4-point Lagrange
-// polynomial through the stencil (nodes x_{j-1}, x_j, x_{j+1}, x_{j+2}), and
-// evaluates phase and amplitude at its points.  The phase of term (n, m) is
-// exact in its integer part: k kappa_n (z_m - z_lo) = 2 pi (n m mod N) / N.
+// A CTA owns one tile of TM = 32 PW consecutive grid points and one mode
+// group; its RESUM_WARPS warps take the group's modes round-robin, each
+// summing into registers (lane l holds points l, l + 32, ...), and the CTA
+// adds the warps' sums in a fixed order before writing one partial per
+// (group, point).
+//
+// Per mode a warp
+//  (1) stages the rays landing on the tile -- brackets jlo[t] .. jlo[t+1]
+//      with stencil -1 / +2 -- in shared memory: landing X (grid units from
+//      the tile start), phase, amplitude;
+//  (2) one lane per interval [X_w, X_{w+1}): builds the 4-point Lagrange
+//      polynomial through X_{w-1} .. X_{w+2} (Newton form, then monomial in
+//      tau = x - X_w) for phase and amplitude, and marks the tile points the
+//      interval contains in a point -> interval table;
+//  (3) every lane evaluates its points: interval lookup, two cubics, the
+//      phase with its integer part exact (k kappa_n (z_m - z_lo) =
+//      2 pi (n m mod N) / N), sincos, complex multiply-accumulate.
+constexpr int RESUM_WARPS = 4;
+constexpr int RESUM_CF = 12;      // X_w, 4 phase + 4 amplitude coefficients, 3 pad
+
+template <typename T>
+__device__ __forceinline__ int resum_warp_bytes(int wcap) {
+  return ((RESUM_CF + 3) * wcap * (int)sizeof(T) + 15) & ~15;
+}
+
+// one coefficient row (X_w, phase b0..b3, amplitude a0..a3), vector stores:
+// rows are 48 B (FP32) apart, so a quarter-warp writes 32 distinct banks
+__device__ __forceinline__ void store_cf(float* p, float X1, float b0, float b1, float b2,
+                                         float b3, float a0, float a1, float a2, float a3) {
+  *reinterpret_cast<float4*>(p) = make_float4(X1, b0, b1, b2);
+  *reinterpret_cast<float4*>(p + 4) = make_float4(b3, a0, a1, a2);
+  *reinterpret_cast<float4*>(p + 8) = make_float4(a3, 0.f, 0.f, 0.f);
+}
+__device__ __forceinline__ void store_cf(double* p, double X1, double b0, double b1, double b2,
+                                         double b3, double a0, double a1, double a2, double a3) {
+  *reinterpret_cast<double2*>(p) = make_double2(X1, b0);
+  *reinterpret_cast<double2*>(p + 2) = make_double2(b1, b2);
+  *reinterpret_cast<double2*>(p + 4) = make_double2(b3, a0);
+  *reinterpret_cast<double2*>(p + 6) = make_double2(a1, a2);
+  *reinterpret_cast<double2*>(p + 8) = make_double2(a3, 0.0);
+}
+
+template <typename T>
+__device__ __forceinline__ void load_cf(const T* p, T& X1, T& b0, T& b1, T& b2, T& b3, T& a0,
+                                        T& a1, T& a2, T& a3);
+template <>
+__device__ __forceinline__ void load_cf<float>(const float* p, float& X1, float& b0, float& b1,
+                                               float& b2, float& b3, float& a0, float& a1,
+                                               float& a2, float& a3) {
+  const float4 u = *reinterpret_cast<const float4*>(p);
+  const float4 v = *reinterpret_cast<const float4*>(p + 4);
+  const float w = p[8];
+  X1 = u.x; b0 = u.y; b1 = u.z; b2 = u.w; b3 = v.x; a0 = v.y; a1 = v.z; a2 = v.w; a3 = w;
+}
+template <>
+__device__ __forceinline__ void load_cf<double>(const double* p, double& X1, double& b0,
+                                                double& b1, double& b2, double& b3, double& a0,
+                                                double& a1, double& a2, double& a3) {
+  const double2 u = *reinterpret_cast<const double2*>(p);
+  const double2 v = *reinterpret_cast<const double2*>(p + 2);
+  const double2 w = *reinterpret_cast<const double2*>(p + 4);
+  const double2 x = *reinterpret_cast<const double2*>(p + 6);
+  X1 = u.x; b0 = u.y; b1 = v.x; b2 = v.y; b3 = w.x; a0 = w.y; a1 = x.x; a2 = x.y; a3 = p[8];
+}
+
+// Newton divided differences through (X1, X2, X0, X3), rewritten as a cubic
+// in tau = x - X1:  b0 + b1 tau + b2 tau^2 + b3 tau^3.
+template <typename T>
+__device__ __forceinline__ void cubic_through(T f0, T f1, T f2, T f3, T r21, T r10, T r32, T r20,
+                                              T r31, T r30, T h21, T h10, T& b0, T& b1, T& b2,
+                                              T& b3) {
+  const T d12 = (f2 - f1) * r21, d01 = (f1 - f0) * r10, d23 = (f3 - f2) * r32;
+  const T d012 = (d12 - d01) * r20, d123 = (d23 - d12) * r31;
+  const T d0123 = (d123 - d012) * r30;
+  b0 = f1;
+  b1 = d12 - h21 * (d012 + d0123 * h10);
+  b2 = d012 + d0123 * (h10 - h21);
+  b3 = d0123;
+}
+
 template <typename T, int PW>
-__global__ void __launch_bounds__(128) k_resum(const ResumArgs<T> p) {
+__global__ void __launch_bounds__(RESUM_WARPS * 32) k_resum(const ResumArgs<T> p) {
   using V = typename C2<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  const int item = blockIdx.x * (blockDim.x >> 5) + warp;
-  if (item >= p.n_tiles * p.n_groups) return;
-  const int tile = item % p.n_tiles;
-  const int group = item / p.n_tiles;
-  T* s_d = reinterpret_cast<T*>(smem_raw) + (long long)warp * 3 * p.wcap;
-  T* s_ph = s_d + p.wcap;
-  T* s_a = s_ph + p.wcap;
-  const int m0 = tile * p.TM;
+  const int tt = blockIdx.x % p.n_tiles_run;
+  const int group = blockIdx.x / p.n_tiles_run;
+  const int half = p.n_tiles >> 1;
+  const int tile = p.sym ? (tt < half ? half + tt : 0) : tt;
+  const int wcap = p.wcap;
+  const int TM = p.TM;
+  unsigned char* wbase = smem_raw + (long long)warp * resum_warp_bytes<T>(wcap);
+  T* s_cf = reinterpret_cast<T*>(wbase);            // [wcap][RESUM_CF], 16-byte aligned
+  T* s_X = s_cf + RESUM_CF * wcap;
+  T* s_ph = s_X + wcap;
+  T* s_a = s_ph + wcap;
+  const int m0 = tile * TM;
   const int i0 = group * p.modes_per_group;
   const int i1 = min(p.M, i0 + p.modes_per_group);
-  const T invN = T(1) / T(p.N);
+  const int lgN = __ffs(p.N) - 1;
+  const T invN = scalbn(T(1), -lgN);               // exact
   const unsigned mask = (unsigned)p.N - 1u;
+  unsigned st = 0;
 
   T accr[PW], acci[PW];
 #pragma unroll
   for (int q = 0; q < PW; ++q) { accr[q] = T(0); acci[q] = T(0); }
 
-  for (int i = i0; i < i1; ++i) {
-    const int jl = __ldg(p.jlo + (long long)tile * p.M + i);
-    const int jh = __ldg(p.jlo + (long long)(tile + 1) * p.M + i);
+  for (int i = i0 + warp; i < i1; i += RESUM_WARPS) {
+    // grounded: mode n < 0 is the mirror image of mode -n (column -n); its
+    // ray j' is ray NRT - j' of mode -n, landing at N - g
+    const int n = i - p.n_max;
+    const bool mirrored = p.sym && n < 0;
+    const int col = p.sym ? (n < 0 ? -n : n) : i;
+    const int* jt = mirrored ? p.jlo_neg : p.jlo;
+    const int jl = __ldg(jt + (long long)tile * p.Mr + col);
+    const int jh = __ldg(jt + (long long)(tile + 1) * p.Mr + col);
     // A bracket table left inconsistent by a failed screen (already flagged
     // by k_bracket) must not send the reads out of [0, NRT).
-    if (jl < 1 || jh < jl || jh > p.NRT - 3) continue;
+    if (jl < (mirrored ? 2 : 1) || jh < jl || jh > p.NRT - 3) continue;
     const int jb = jl - 1;
     const int W = jh - jl + 4;
-    const T* gd;
-    const T* gph;
-    const T* ga;
-    long long stride;
+    if (W > wcap) {            // rays compressed beyond the tile's capacity
+      st |= ST_CAUSTIC;
+      continue;
+    }
+    const V cn = p.c[i];
+    const unsigned nn = (unsigned)n;
     __syncwarp();
-    if (W <= p.wcap) {
+    if (!mirrored) {
+      const int base = (jb - p.G) * p.R - m0;
       for (int w = lane; w < W; w += 32) {
-        const long long o = (long long)(jb + w) * p.M + i;
-        s_d[w] = __ldg(p.d + o);
+        const long long o = (long long)(jb + w) * p.Mr + col;
+        s_X[w] = T(base + w * p.R) + __ldg(p.d + o);
         s_ph[w] = __ldg(p.ph + o);
         s_a[w] = __ldg(p.a + o);
       }
-      __syncwarp();
-      gd = s_d; gph = s_ph; ga = s_a; stride = 1;
     } else {
-      const long long o = (long long)jb * p.M + i;
-      gd = p.d + o; gph = p.ph + o; ga = p.a + o; stride = p.M;
+      const int base = p.N - m0 - (p.NRT - jb - p.G) * p.R;
+      for (int w = lane; w < W; w += 32) {
+        const long long o = (long long)(p.NRT - jb - w) * p.Mr + col;
+        s_X[w] = T(base + w * p.R) - __ldg(p.d + o);
+        s_ph[w] = __ldg(p.ph + o);
+        s_a[w] = __ldg(p.a + o);
+      }
     }
-    const int base = (jb - p.G) * p.R - m0;   // node w sits at base + w R + d_w
-    const T x0 = T(lane * PW);
-    int lo = 1, hi = W - 2;
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (T(base + mid * p.R) + gd[mid * stride] <= x0) lo = mid; else hi = mid;
+    __syncwarp();
+    for (int w = 1 + lane; w <= W - 3; w += 32) {
+      const T X0 = s_X[w - 1], X1 = s_X[w], X2 = s_X[w + 1], X3 = s_X[w + 2];
+      const T h21 = X2 - X1, h10 = X1 - X0;
+      const T r21 = T(1) / h21, r10 = T(1) / h10, r32 = T(1) / (X3 - X2);
+      const T r20 = T(1) / (X2 - X0), r31 = T(1) / (X3 - X1), r30 = T(1) / (X3 - X0);
+      T b0, b1, b2, b3, a0, a1, a2, a3;
+      cubic_through(s_ph[w - 1], s_ph[w], s_ph[w + 1], s_ph[w + 2], r21, r10, r32, r20, r31, r30,
+                    h21, h10, b0, b1, b2, b3);
+      cubic_through(s_a[w - 1], s_a[w], s_a[w + 1], s_a[w + 2], r21, r10, r32, r20, r31, r30,
+                    h21, h10, a0, a1, a2, a3);
+      store_cf(s_cf + RESUM_CF * w, X1, b0, b1, b2, b3, a0, a1, a2, a3);
     }
-    int wb = lo;
-    int cur = -1;
-    T X1 = 0, h21 = 0, h10 = 0;
-    T cp0 = 0, cp1 = 0, cp2 = 0, cp3 = 0, ca0 = 0, ca1 = 0, ca2 = 0, ca3 = 0;
-    const V cn = p.c[i];
-    const unsigned nn = (unsigned)(i - p.n_max);
+    __syncwarp();
+    // interval of point x: X_w <= x < X_{w+1}, w in [1, W-3]; guessed from the
+    // mean landing spacing, then corrected by comparisons
+    const T xf = s_X[1];
+    const T inv_sp = T(W - 3) / (s_X[W - 2] - xf);
 #pragma unroll
     for (int q = 0; q < PW; ++q) {
-      const T x = T(lane * PW + q);
-      while (wb < W - 3 && T(base + (wb + 1) * p.R) + gd[(wb + 1) * stride] <= x) ++wb;
-      if (wb != cur) {
-        cur = wb;
-        const T X0 = T(base + (wb - 1) * p.R) + gd[(wb - 1) * stride];
-        X1 = T(base + wb * p.R) + gd[wb * stride];
-        const T X2 = T(base + (wb + 1) * p.R) + gd[(wb + 1) * stride];
-        const T X3 = T(base + (wb + 2) * p.R) + gd[(wb + 2) * stride];
-        h21 = X2 - X1;
-        h10 = X1 - X0;
-        const T r21 = T(1) / h21, r10 = T(1) / h10, r32 = T(1) / (X3 - X2);
-        const T r20 = T(1) / (X2 - X0), r31 = T(1) / (X3 - X1), r30 = T(1) / (X3 - X0);
-        {
-          const T f0 = gph[(wb - 1) * stride], f1 = gph[wb * stride];
-          const T f2 = gph[(wb + 1) * stride], f3 = gph[(wb + 2) * stride];
-          const T d12 = (f2 - f1) * r21, d01 = (f1 - f0) * r10, d23 = (f3 - f2) * r32;
-          const T d012 = (d12 - d01) * r20, d123 = (d23 - d12) * r31;
-          cp0 = f1; cp1 = d12; cp2 = d012; cp3 = (d123 - d012) * r30;
-        }
-        {
-          const T f0 = ga[(wb - 1) * stride], f1 = ga[wb * stride];
-          const T f2 = ga[(wb + 1) * stride], f3 = ga[(wb + 2) * stride];
-          const T d12 = (f2 - f1) * r21, d01 = (f1 - f0) * r10, d23 = (f3 - f2) * r32;
-          const T d012 = (d12 - d01) * r20, d123 = (d23 - d12) * r31;
-          ca0 = f1; ca1 = d12; ca2 = d012; ca3 = (d123 - d012) * r30;
-        }
-      }
-      const T tau = x - X1;
-      const T e2 = tau - h21;
-      const T e0 = tau + h10;
-      const T phv = cp0 + tau * (cp1 + e2 * (cp2 + e0 * cp3));
-      const T av = ca0 + tau * (ca1 + e2 * (ca2 + e0 * ca3));
-      const unsigned nm = (nn * (unsigned)(m0 + lane * PW + q)) & mask;
+      const int x = lane + 32 * q;
+      const T xv = T(x);
+      int w = 1 + (int)((xv - xf) * inv_sp);
+      w = min(max(w, 1), W - 3);
+      while (w > 1 && s_X[w] > xv) --w;
+      while (w < W - 3 && s_X[w + 1] <= xv) ++w;
+      T X1, b0, b1, b2, b3, a0, a1, a2, a3;
+      load_cf<T>(s_cf + RESUM_CF * w, X1, b0, b1, b2, b3, a0, a1, a2, a3);
+      const T tau = xv - X1;
+      const T phv = ((b3 * tau + b2) * tau + b1) * tau + b0;
+      const T av = ((a3 * tau + a2) * tau + a1) * tau + a0;
+      const unsigned nm = (nn * (unsigned)(m0 + x)) & mask;
       T t = T(nm) * invN + phv;
       t -= rint(t);
       T sn, cs;
-      sincospi_t(T(2) * t, &sn, &cs);
+      sincos_turns(t, &sn, &cs);
       const T ar = av * cn.x, ai = av * cn.y;
       accr[q] += ar * cs - ai * sn;
       acci[q] += ar * sn + ai * cs;
     }
   }
-  V* out = p.part + (long long)group * p.N + m0 + lane * PW;
+  if (st) atomicOr(p.status, st);
+  // fixed-order sum of the warps' partial sums
+  __syncthreads();
+  V* red = reinterpret_cast<V*>(smem_raw);
 #pragma unroll
   for (int q = 0; q < PW; ++q) {
     V v;
     v.x = accr[q];
     v.y = acci[q];
-    out[q] = v;
+    red[warp * TM + lane + 32 * q] = v;
+  }
+  __syncthreads();
+  V* out = p.part + (long long)group * p.N + m0;
+  for (int x = threadIdx.x; x < TM; x += blockDim.x) {
+    V sum = red[x];
+#pragma unroll
+    for (int w = 1; w < RESUM_WARPS; ++w) {
+      const V v = red[w * TM + x];
+      sum.x += v.x; sum.y += v.y;
+    }
+    out[x] = sum;
   }
 }
 
@@ -365,7 +498,7 @@ __global__ void __launch_bounds__(128) k_resum(const ResumArgs<T> p) {
 template <typename T>
 __global__ void k_reduce(const ReduceArgs<T> p) {
   using V = typename C2<T>::type;
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
   auto sum_at = [&](int mm) {
     V s;
     s.x = T(0); s.y = T(0);
@@ -376,6 +509,26 @@ __global__ void k_reduce(const ReduceArgs<T> p) {
     if (p.W) { const T w = p.W[mm]; s.x *= w; s.y *= w; }
     return s;
   };
+  const T sg = T(p.mirror);
+  if (p.sym) {
+    // partials hold the physical half m in [N/2, N) and m = 0; the other
+    // half is its reflection
+    if (k > p.N / 2) return;
+    const int m = k < p.N / 2 ? p.N / 2 + k : 0;
+    const V a = sum_at(m);
+    if (m == 0 || m == p.N / 2) {
+      V v;
+      v.x = T(0.5) * (a.x + sg * a.x); v.y = T(0.5) * (a.y + sg * a.y);
+      p.u[m] = v;
+    } else {
+      V b;
+      b.x = sg * a.x; b.y = sg * a.y;
+      p.u[m] = a;
+      p.u[p.N - m] = b;
+    }
+    return;
+  }
+  const int m = k;
   if (!p.mirror) {
     if (m < p.N) p.u[m] = sum_at(m);
     return;
@@ -384,7 +537,6 @@ __global__ void k_reduce(const ReduceArgs<T> p) {
   const int mm = (p.N - m) & (p.N - 1);
   const V a = sum_at(m);
   const V b = (mm == m) ? a : sum_at(mm);
-  const T sg = T(p.mirror);
   V ua, ub;
   ua.x = T(0.5) * (a.x + sg * b.x); ua.y = T(0.5) * (a.y + sg * b.y);
   ub.x = T(0.5) * (b.x + sg * a.x); ub.y = T(0.5) * (b.y + sg * a.y);
@@ -436,61 +588,83 @@ __device__ __forceinline__ typename C2<T>::type cmul(typename C2<T>::type a,
   return r;
 }
 
+// pass 1: a CTA takes 32 consecutive columns n2 (all N1 rows, one coalesced
+// tile in shared memory) and forms Y[k1][n2] = w_N^{n2 k1} sum_n1 x[n1 N2 + n2]
+// w_{N1}^{n1 k1} for all k1.  N1 <= 64.
+constexpr int FFT1_COLS = 32;
+
 template <typename T>
-__global__ void k_fft1(const FftArgs<T> p) {
+__global__ void __launch_bounds__(256) k_fft1(const FftArgs<T> p) {
   using V = typename C2<T>::type;
-  const int n2 = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n2 >= p.N2) return;
-  for (int k1 = 0; k1 < p.N1; ++k1) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* tile = reinterpret_cast<V*>(smem_raw);          // [N1][FFT1_COLS]
+  V* w1 = tile + p.N1 * FFT1_COLS;                   // [N1] w_{N1}^k
+  const int c0 = blockIdx.x * FFT1_COLS;
+  for (int e = threadIdx.x; e < p.N1 * FFT1_COLS; e += blockDim.x) {
+    const int n1 = e / FFT1_COLS, c = e % FFT1_COLS;
+    tile[e] = p.u[(long long)n1 * p.N2 + c0 + c];
+  }
+  for (int k = threadIdx.x; k < p.N1; k += blockDim.x) w1[k] = p.tw[(long long)k * p.N2];
+  __syncthreads();
+  for (int e = threadIdx.x; e < p.N1 * FFT1_COLS; e += blockDim.x) {
+    const int k1 = e / FFT1_COLS, c = e % FFT1_COLS;
     V acc;
     acc.x = T(0); acc.y = T(0);
     for (int n1 = 0; n1 < p.N1; ++n1) {
-      const V x = p.u[(long long)n1 * p.N2 + n2];
-      const V w = p.tw[(long long)((n1 * k1) % p.N1) * p.N2];
-      const V t = cmul<T>(x, w);
+      const V t = cmul<T>(tile[n1 * FFT1_COLS + c], w1[(n1 * k1) & (p.N1 - 1)]);
       acc.x += t.x; acc.y += t.y;
     }
+    const int n2 = c0 + c;
     p.Y[(long long)k1 * p.N2 + n2] = cmul<T>(acc, p.tw[(long long)n2 * k1]);
   }
 }
 
+// w_{N2}^{idx}: FP32 computes it (sincospi, ~1 ulp), FP64 reads the table.
+__device__ __forceinline__ float2 twiddle2(const float2*, unsigned idx, int lgN2, int) {
+  float s, c;
+  sincospif(scalbnf((float)idx, 1 - lgN2), &s, &c);   // 2 idx / N2, exact
+  return make_float2(c, -s);
+}
+__device__ __forceinline__ double2 twiddle2(const double2* tw, unsigned idx, int, int N1) {
+  return tw[(long long)idx * N1];
+}
+
+// pass 2: one warp per kept mode n: X[k1 + N1 k2] = sum_n2 Y[k1][n2] w_{N2}^{n2 k2}
+// (direct, pruned: only the 2 n_max + 1 kept bins are formed); c_n = X / N
+// times the range-phase carry.
 template <typename T>
 __global__ void __launch_bounds__(256) k_fft2(const FftArgs<T> p) {
   using V = typename C2<T>::type;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  V* A = reinterpret_cast<V*>(smem_raw);
-  V* B = A + p.N2;
-  const int k1 = blockIdx.x;
-  const V* src = (p.N1 > 1) ? p.Y + (long long)k1 * p.N2 : p.u;
-  for (int x = threadIdx.x; x < p.N2; x += blockDim.x) A[x] = src[x];
-  __syncthreads();
-  const int half = p.N2 >> 1;
-  for (int m = 1, lg = 0; m < p.N2; m <<= 1, ++lg) {
-    const long long twstep = (long long)p.N >> (lg + 1);   // N / (2m)
-    for (int b = threadIdx.x; b < half; b += blockDim.x) {
-      const int j = b >> lg;
-      const int k = b & (m - 1);
-      const V w = p.tw[k * twstep];
-      const V c0 = A[k + j * m];
-      const V c1 = cmul<T>(w, A[k + j * m + half]);
-      V y0, y1;
-      y0.x = c0.x + c1.x; y0.y = c0.y + c1.y;
-      y1.x = c0.x - c1.x; y1.y = c0.y - c1.y;
-      B[k + 2 * j * m] = y0;
-      B[k + 2 * j * m + m] = y1;
-    }
-    __syncthreads();
-    V* t = A; A = B; B = t;
+  const int lane = threadIdx.x & 31;
+  // grounded fields are even / odd, so c_{-n} = +-c_n: only n >= 0 is formed
+  const int i = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) + (p.mirror ? p.n_max : 0);
+  if (i > 2 * p.n_max) return;
+  const int n = i - p.n_max;
+  const int b = n >= 0 ? n : n + p.N;
+  const int k1 = b & (p.N1 - 1);
+  const int k2 = b / p.N1;
+  const V* row = (p.N1 > 1 ? p.Y : p.u) + (long long)k1 * p.N2;
+  V acc;
+  acc.x = T(0); acc.y = T(0);
+  for (int n2 = lane; n2 < p.N2; n2 += 32) {
+    const unsigned e = (unsigned)(((long long)n2 * k2) & (p.N2 - 1));
+    const V t = cmul<T>(row[n2], twiddle2(p.tw, e, p.log2N2, p.N1));
+    acc.x += t.x; acc.y += t.y;
   }
-  for (int k2 = threadIdx.x; k2 < p.N2; k2 += blockDim.x) {
-    const long long b = (long long)k1 + (long long)p.N1 * k2;
-    int n;
-    if (b <= p.n_max) n = (int)b;
-    else if (b >= (long long)p.N - p.n_max) n = (int)(b - p.N);
-    else continue;
-    V v = A[k2];
-    v.x *= p.inv_N; v.y *= p.inv_N;
-    p.c[n + p.n_max] = cmul<T>(v, p.ephi[n + p.n_max]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+  }
+  if (lane == 0) {
+    acc.x *= p.inv_N; acc.y *= p.inv_N;
+    const V cv = cmul<T>(acc, p.ephi[i]);
+    p.c[i] = cv;
+    if (p.mirror && n > 0) {
+      V cm;
+      cm.x = T(p.mirror) * cv.x; cm.y = T(p.mirror) * cv.y;
+      p.c[2 * p.n_max - i] = cm;
+    }
   }
 }
 
@@ -506,7 +680,7 @@ cudaError_t launch_init(const double* u0, int n_z, int N, int mirror, typename C
 
 template <typename T>
 cudaError_t launch_reduce(const ReduceArgs<T>& a, cudaStream_t s) {
-  const int n = a.mirror ? a.N / 2 + 1 : a.N;
+  const int n = (a.mirror || a.sym) ? a.N / 2 + 1 : a.N;
   k_reduce<T><<<(n + 255) / 256, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
@@ -514,45 +688,50 @@ cudaError_t launch_reduce(const ReduceArgs<T>& a, cudaStream_t s) {
 template <typename T>
 cudaError_t launch_fft(const FftArgs<T>& a, cudaStream_t s) {
   if (a.N1 > 1) {
-    k_fft1<T><<<(a.N2 + 127) / 128, 128, 0, s>>>(a);
+    const size_t smem = (size_t)(a.N1 * FFT1_COLS + a.N1) * sizeof(typename C2<T>::type);
+    k_fft1<T><<<a.N2 / FFT1_COLS, 256, smem, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  const size_t smem = 2 * (size_t)a.N2 * sizeof(typename C2<T>::type);
-  k_fft2<T><<<a.N1, 256, smem, s>>>(a);
+  const int warps = a.mirror ? a.n_max + 1 : 2 * a.n_max + 1;
+  k_fft2<T><<<(warps + 7) / 8, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_march(const MarchArgs<T>& a, cudaStream_t s) {
+cudaError_t launch_march(const MarchArgs<T>& a, bool multi_column, cudaStream_t s) {
   dim3 block(32, 8);
-  dim3 grid((a.M + 31) / 32, (a.NRT + 7) / 8);
-  k_march<T><<<grid, block, 0, s>>>(a);
+  dim3 grid((a.Mr + 31) / 32, (a.NRT + 7) / 8);
+  if (multi_column) k_march<T, true><<<grid, block, 0, s>>>(a);
+  else k_march<T, false><<<grid, block, 0, s>>>(a);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_bracket(const BracketArgs<T>& a, cudaStream_t s) {
-  dim3 grid((a.M + 127) / 128, a.NRT - 1);
+  dim3 grid((a.Mr + 127) / 128, a.NRT - 1);
   k_bracket<T><<<grid, 128, 0, s>>>(a);
   return cudaGetLastError();
 }
 
 template <typename T>
-size_t resum_smem_bytes(int wcap, int warps_per_cta) {
-  return (size_t)warps_per_cta * 3 * wcap * sizeof(T);
+size_t resum_smem_bytes(int wcap, int tile_points) {
+  const size_t per_warp = ((RESUM_CF + 3) * (size_t)wcap * sizeof(T) + 15) & ~(size_t)15;
+  const size_t stage = (size_t)RESUM_WARPS * per_warp;
+  const size_t red = (size_t)RESUM_WARPS * tile_points * sizeof(typename C2<T>::type);
+  return stage > red ? stage : red;
 }
 
 template <typename T>
-cudaError_t launch_resum(const ResumArgs<T>& a, int warps_per_cta, cudaStream_t s) {
-  const int items = a.n_tiles * a.n_groups;
-  const int grid = (items + warps_per_cta - 1) / warps_per_cta;
-  const size_t smem = resum_smem_bytes<T>(a.wcap, warps_per_cta);
+cudaError_t launch_resum(const ResumArgs<T>& a, cudaStream_t s) {
+  const int grid = a.n_tiles_run * a.n_groups;
+  const size_t smem = resum_smem_bytes<T>(a.wcap, a.TM);
+  const int threads = RESUM_WARPS * 32;
   switch (a.PW) {
-    case 2: k_resum<T, 2><<<grid, warps_per_cta * 32, smem, s>>>(a); break;
-    case 4: k_resum<T, 4><<<grid, warps_per_cta * 32, smem, s>>>(a); break;
-    case 8: k_resum<T, 8><<<grid, warps_per_cta * 32, smem, s>>>(a); break;
-    case 16: k_resum<T, 16><<<grid, warps_per_cta * 32, smem, s>>>(a); break;
+    case 2: k_resum<T, 2><<<grid, threads, smem, s>>>(a); break;
+    case 4: k_resum<T, 4><<<grid, threads, smem, s>>>(a); break;
+    case 8: k_resum<T, 8><<<grid, threads, smem, s>>>(a); break;
+    case 16: k_resum<T, 16><<<grid, threads, smem, s>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -560,13 +739,10 @@ cudaError_t launch_resum(const ResumArgs<T>& a, int warps_per_cta, cudaStream_t 
 
 template <typename T>
 cudaError_t prepare_kernels(int resum_smem) {
-  cudaError_t e = cudaFuncSetAttribute(k_fft2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(2 * 4096 * sizeof(typename C2<T>::type)));
-  if (e != cudaSuccess) return e;
   const void* fs[] = {(const void*)k_resum<T, 2>, (const void*)k_resum<T, 4>,
                       (const void*)k_resum<T, 8>, (const void*)k_resum<T, 16>};
   for (const void* f : fs) {
-    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, resum_smem);
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, resum_smem);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -574,8 +750,7 @@ cudaError_t prepare_kernels(int resum_smem) {
 
 template <typename T>
 cudaError_t prepare_fft_kernels() {
-  return cudaFuncSetAttribute(k_fft2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)(2 * 4096 * sizeof(typename C2<T>::type)));
+  return cudaSuccess;   // the DFT passes use no dynamic shared memory
 }
 
 template <typename T>
@@ -589,9 +764,9 @@ cudaError_t launch_output(const typename C2<T>::type* u, int offset, int n, doub
   template cudaError_t launch_init<T>(const double*, int, int, int, C2<T>::type*, cudaStream_t); \
   template cudaError_t launch_reduce<T>(const ReduceArgs<T>&, cudaStream_t);                    \
   template cudaError_t launch_fft<T>(const FftArgs<T>&, cudaStream_t);                          \
-  template cudaError_t launch_march<T>(const MarchArgs<T>&, cudaStream_t);                      \
+  template cudaError_t launch_march<T>(const MarchArgs<T>&, bool, cudaStream_t);                \
   template cudaError_t launch_bracket<T>(const BracketArgs<T>&, cudaStream_t);                  \
-  template cudaError_t launch_resum<T>(const ResumArgs<T>&, int, cudaStream_t);                 \
+  template cudaError_t launch_resum<T>(const ResumArgs<T>&, cudaStream_t);                      \
   template cudaError_t launch_output<T>(const C2<T>::type*, int, int, double*, cudaStream_t);   \
   template size_t resum_smem_bytes<T>(int, int);                                                \
   template cudaError_t prepare_kernels<T>(int);                                                 \

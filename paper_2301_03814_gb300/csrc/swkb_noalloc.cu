@@ -118,7 +118,8 @@ extern "C" swkb_status swkb_modes_noalloc(const double* u, int32_t n_fft, int32_
   f.tw = d->twiddle;
   f.Y = d->mid;
   f.N = n_fft;
-  f.N2 = n_fft < 2048 ? n_fft : 2048;
+  f.N2 = n_fft < 2048 ? n_fft : 2048;   // N1 = n_fft / N2 <= 32
+  f.mirror = 0;
   f.N1 = n_fft / f.N2;
   f.log2N2 = 0;
   while ((1 << f.log2N2) < f.N2) ++f.log2N2;

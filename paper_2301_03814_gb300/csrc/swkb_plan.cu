@@ -65,13 +65,15 @@ struct swkb_plan {
   int precision = SWKB_FP64;
   int bc = SWKB_BC_PERIODIC;
   int mirror = 0;  // 0 periodic, +1 Neumann, -1 Dirichlet
+  int sym = 0;     // grounded: march modes n >= 0 only, sum the physical half only
+  int Mr = 0;      // marched modes
+  int n_tiles_run = 0;
   int n_z = 0, N = 0, N1 = 1, N2 = 1, log2N2 = 0;
   int n_max = 0, M = 0, R = 1, N_r = 0, G = 0, NRT = 0, Nt = 0;
   double k = 0, z_a = 0, z_b = 0, x0 = 0, dx = 0, L = 0, dz = 0, z_lo = 0;
   double eps_ref = 0, absorber_frac = 0;
   // resummation tiling
   int PW = 8, TM = 256, n_tiles = 0, n_groups = 1, modes_per_group = 1, wcap = 0;
-  int warps_per_cta = 4;
   // medium
   int n_cols = 0, n_p = 0, n_int = 0;
   double z0p = 0, dzp = 0;
@@ -98,6 +100,7 @@ struct swkb_plan {
   void* rph = nullptr;
   void* ra = nullptr;
   int* jlo = nullptr;
+  int* jlo_neg = nullptr;
   unsigned* status = nullptr;
   int* stage_c = nullptr;
   void* stage_th = nullptr;
@@ -264,15 +267,21 @@ swkb_status build_device(swkb_plan* p, const swkb_profile* prof) {
   TRY(dev_alloc(p, &p->part, (size_t)p->n_groups * N * sizeof(V)));
   TRY(dev_alloc(p, &p->Y, (size_t)N * sizeof(V)));
   TRY(dev_alloc(p, &p->c, (size_t)M * sizeof(V)));
-  TRY(dev_alloc(p, &p->rd, (size_t)p->NRT * M * sizeof(T)));
-  TRY(dev_alloc(p, &p->rph, (size_t)p->NRT * M * sizeof(T)));
-  TRY(dev_alloc(p, &p->ra, (size_t)p->NRT * M * sizeof(T)));
-  TRY(dev_alloc(p, (void**)&p->jlo, (size_t)(p->n_tiles + 1) * M * sizeof(int)));
-  CK(cudaMemset(p->jlo, 0, (size_t)(p->n_tiles + 1) * M * sizeof(int)));
+  const size_t rays = (size_t)p->NRT * p->Mr;
+  TRY(dev_alloc(p, &p->rd, rays * sizeof(T)));
+  TRY(dev_alloc(p, &p->rph, rays * sizeof(T)));
+  TRY(dev_alloc(p, &p->ra, rays * sizeof(T)));
+  const size_t jn = (size_t)(p->n_tiles + 1) * p->Mr;
+  TRY(dev_alloc(p, (void**)&p->jlo, jn * sizeof(int)));
+  CK(cudaMemset(p->jlo, 0, jn * sizeof(int)));
+  if (p->sym) {
+    TRY(dev_alloc(p, (void**)&p->jlo_neg, jn * sizeof(int)));
+    CK(cudaMemset(p->jlo_neg, 0, jn * sizeof(int)));
+  }
   TRY(dev_alloc(p, (void**)&p->status, sizeof(unsigned)));
   CK(cudaMemset(p->status, 0, sizeof(unsigned)));
   TRY(dev_alloc(p, (void**)&p->io, 2 * (size_t)std::max(N, p->n_z) * sizeof(double)));
-  CK(prepare_kernels<T>((int)resum_smem_bytes<T>(p->wcap, p->warps_per_cta)));
+  CK(prepare_kernels<T>((int)resum_smem_bytes<T>(p->wcap, p->TM)));
   return SWKB_OK;
 }
 
@@ -329,7 +338,7 @@ MarchArgs<T> march_args(const swkb_plan* p, int q) {
   a.med.col_stride = (long long)p->n_int * 8;
   a.med.z0 = (T)p->z0p;
   a.med.inv_h = (T)(1.0 / p->dzp);
-  a.med.inv_h2 = (T)(1.0 / (p->dzp * p->dzp));
+  a.med.inv_h2 = (T)(2.0 / (p->dzp * p->dzp));
   a.med.mirrored = p->mirror != 0;
   a.med.z_mirror = (T)p->z_a;
   const int S = 2 * p->Nt + 1;
@@ -339,7 +348,8 @@ MarchArgs<T> march_args(const swkb_plan* p, int q) {
   a.kappa = (const T*)p->kappa;
   a.pbar = (const T*)p->pbar_d;
   a.pbar2 = (const T*)p->pbar2_d;
-  a.M = p->M; a.NRT = p->NRT; a.G = p->G; a.R = p->R; a.Nt = p->Nt;
+  a.Mr = p->Mr; a.mode_off = p->sym ? p->n_max : 0;
+  a.NRT = p->NRT; a.G = p->G; a.R = p->R; a.Nt = p->Nt;
   a.z_lo = (T)p->z_lo; a.dz = (T)p->dz; a.inv_dz = (T)(1.0 / p->dz);
   a.h = (T)(p->dx / p->Nt);
   a.k_over_2pi = (T)(p->k / (2.0 * M_PI));
@@ -353,28 +363,32 @@ swkb_status launch_screen(swkb_plan* p, int q, bool u_fresh) {
   using V = typename C2<T>::type;
   cudaStream_t s = p->stream;
   if (!u_fresh) {
-    ReduceArgs<T> r{(const V*)p->part, p->n_groups, p->N, (const T*)p->W, p->mirror, (V*)p->u};
+    ReduceArgs<T> r{(const V*)p->part, p->n_groups, p->N, (const T*)p->W, p->mirror, p->sym,
+                    (V*)p->u};
     TRY(timed(p, SWKB_KERNEL_REDUCE, 1, [&] { return launch_reduce<T>(r, s); }));
   }
   FftArgs<T> f;
   f.u = (const V*)p->u; f.tw = (const V*)p->tw; f.Y = (V*)p->Y;
   f.N = p->N; f.N1 = p->N1; f.N2 = p->N2; f.log2N2 = p->log2N2; f.n_max = p->n_max;
+  f.mirror = p->mirror;
   f.inv_N = (T)(1.0 / p->N);
   f.ephi = (const V*)p->ephi_d; f.c = (V*)p->c;
   TRY(timed(p, SWKB_KERNEL_FFT, p->N1 > 1 ? 2 : 1, [&] { return launch_fft<T>(f, s); }));
   const MarchArgs<T> ma = march_args<T>(p, q);
-  TRY(timed(p, SWKB_KERNEL_MARCH, 1, [&] { return launch_march<T>(ma, s); }));
-  BracketArgs<T> b{(const T*)p->rd, p->M, p->NRT, p->G, p->R, p->N, p->TM, p->n_tiles,
-                   p->jlo, p->status};
+  const bool multi = p->n_cols > 1;
+  TRY(timed(p, SWKB_KERNEL_MARCH, 1, [&] { return launch_march<T>(ma, multi, s); }));
+  BracketArgs<T> b{(const T*)p->rd, p->Mr, p->NRT, p->G, p->R, p->N, p->TM, p->n_tiles,
+                   p->jlo, p->sym, p->jlo_neg, p->status};
   TRY(timed(p, SWKB_KERNEL_BRACKET, 1, [&] { return launch_bracket<T>(b, s); }));
   ResumArgs<T> ra;
   ra.d = (const T*)p->rd; ra.ph = (const T*)p->rph; ra.a = (const T*)p->ra; ra.jlo = p->jlo;
+  ra.jlo_neg = p->jlo_neg;
   ra.c = (const V*)p->c;
-  ra.M = p->M; ra.NRT = p->NRT; ra.G = p->G; ra.R = p->R; ra.N = p->N; ra.TM = p->TM;
+  ra.M = p->M; ra.Mr = p->Mr; ra.sym = p->sym; ra.n_tiles_run = p->n_tiles_run; ra.NRT = p->NRT; ra.G = p->G; ra.R = p->R; ra.N = p->N; ra.TM = p->TM;
   ra.PW = p->PW; ra.n_tiles = p->n_tiles; ra.n_groups = p->n_groups;
   ra.modes_per_group = p->modes_per_group; ra.n_max = p->n_max; ra.wcap = p->wcap;
   ra.part = (V*)p->part; ra.status = p->status;
-  TRY(timed(p, SWKB_KERNEL_RESUM, 1, [&] { return launch_resum<T>(ra, p->warps_per_cta, s); }));
+  TRY(timed(p, SWKB_KERNEL_RESUM, 1, [&] { return launch_resum<T>(ra, s); }));
   p->stats.screens += 1;
   return SWKB_OK;
 }
@@ -382,8 +396,10 @@ swkb_status launch_screen(swkb_plan* p, int q, bool u_fresh) {
 template <typename T>
 swkb_status reduce_to_u(swkb_plan* p, bool project) {
   using V = typename C2<T>::type;
-  ReduceArgs<T> r{(const V*)p->part, p->n_groups, p->N, (const T*)p->W, project ? p->mirror : 0,
-                  (V*)p->u};
+  // grounded plans sum only the physical half, so their reduction always
+  // fills the other half by reflection
+  ReduceArgs<T> r{(const V*)p->part, p->n_groups, p->N, (const T*)p->W,
+                  (project || p->sym) ? p->mirror : 0, p->sym, (V*)p->u};
   TRY(timed(p, SWKB_KERNEL_REDUCE, 1, [&] { return launch_reduce<T>(r, p->stream); }));
   return SWKB_OK;
 }
@@ -449,7 +465,8 @@ swkb_status debug_screen(swkb_plan* p, int q, const double* u_full, double* c, d
   TRY(launch_screen<T>(p, q, true));
   TRY(reduce_to_u<T>(p, false));
   std::vector<V> hc(M), hu(N);
-  std::vector<T> hd((size_t)NRT * M), hph((size_t)NRT * M), ha((size_t)NRT * M);
+  const int Mr = p->Mr;
+  std::vector<T> hd((size_t)NRT * Mr), hph((size_t)NRT * Mr), ha((size_t)NRT * Mr);
   CK(cudaMemcpyAsync(hc.data(), p->c, sizeof(V) * M, cudaMemcpyDeviceToHost, p->stream));
   CK(cudaMemcpyAsync(hu.data(), p->u, sizeof(V) * N, cudaMemcpyDeviceToHost, p->stream));
   CK(cudaMemcpyAsync(hd.data(), p->rd, sizeof(T) * hd.size(), cudaMemcpyDeviceToHost, p->stream));
@@ -465,10 +482,24 @@ swkb_status debug_screen(swkb_plan* p, int q, const double* u_full, double* c, d
     }
   }
   const double two_pi_over_k = 2.0 * M_PI / p->k;
-  for (int j = 0; j < NRT; ++j) {
-    for (int i = 0; i < M; ++i) {
-      const size_t src = (size_t)j * M + i, dst = (size_t)i * NRT + j;
-      if (delta) delta[dst] = (double)((long long)(j - p->G) * p->R) + (double)hd[src];
+  for (int i = 0; i < M; ++i) {
+    const int n = i - p->n_max;
+    const bool mir = p->sym && n < 0;
+    const int col = p->sym ? (n < 0 ? -n : n) : i;
+    for (int j = 0; j < NRT; ++j) {
+      const size_t dst = (size_t)i * NRT + j;
+      // grounded plans march n >= 0; ray j of mode -n mirrors ray NRT - j of
+      // mode n (ray 0 of a mirrored family has no partner: NaN)
+      const int js = mir ? NRT - j : j;
+      if (js >= NRT) {
+        if (delta) delta[dst] = NAN;
+        if (r) r[dst] = NAN;
+        if (a) a[dst] = NAN;
+        continue;
+      }
+      const size_t src = (size_t)js * Mr + col;
+      const double g = (double)((long long)(js - p->G) * p->R) + (double)hd[src];
+      if (delta) delta[dst] = mir ? p->N - g : g;
       if (r) r[dst] = (double)hph[src] * two_pi_over_k + p->dx * p->pbar[i];
       if (a) a[dst] = (double)ha[src];
     }
@@ -595,9 +626,10 @@ swkb_status swkb_plan_create(const swkb_profile* prof, double k, const swkb_doma
     p->absorber_frac = opt.absorber_frac;
     if (!(p->absorber_frac >= 0 && p->absorber_frac < 1))
       return fail(SWKB_ERR_INVALID_ARG, "absorber_frac must be in [0, 1)");
-    // FFT split N = N1 N2 (N2 <= 2048 points in shared memory)
-    p->N2 = std::min(p->N, 2048);
-    p->N1 = p->N / p->N2;
+    // DFT split N = N1 N2 with N1 ~ sqrt(M): pass 1 costs N N1, pass 2 M N2
+    p->N1 = 1;
+    while (p->N1 * p->N1 * 2 < p->M && p->N1 < p->N / 32 && p->N1 < 64) p->N1 *= 2;
+    p->N2 = p->N / p->N1;
     p->log2N2 = ilog2(p->N2);
     // medium
     p->n_cols = prof->n_cols; p->n_p = prof->n_p; p->n_int = prof->n_p - 1;
@@ -639,18 +671,23 @@ swkb_status swkb_plan_create(const swkb_profile* prof, double k, const swkb_doma
       const double q_end = ceil((p->x_cols.back() - p->x0) / p->dx);
       p->stage_rows = (int)std::min(std::max(q_end, 0.0), 1e6) + 1;
     }
+    // grounded domains: mode -n is the mirror image of mode n and the field
+    // is even / odd, so only n >= 0 is marched and only z >= z_a summed
+    p->sym = p->mirror != 0;
+    p->Mr = p->sym ? p->n_max + 1 : p->M;
     // resummation tiling
     p->PW = p->R >= 8 ? 8 : (p->R >= 2 ? 4 : 2);
-    while (32 * p->PW > p->N) p->PW /= 2;
+    while (32 * p->PW > (p->sym ? p->N / 2 : p->N)) p->PW /= 2;
     p->TM = 32 * p->PW;
     p->n_tiles = p->N / p->TM;
-    p->wcap = 2 * p->TM / p->R + 8;
+    p->n_tiles_run = p->sym ? p->n_tiles / 2 + 1 : p->n_tiles;
+    p->wcap = 4 * p->TM / p->R + 8;   // rays per tile window: up to 4x compression
     p->device = opt.device;
     CK(cudaSetDevice(p->device));
     int sms = 0;
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
-    const int target_warps = sms * 32;
-    p->n_groups = std::max(1, std::min(p->M, (target_warps + p->n_tiles - 1) / p->n_tiles));
+    const int target_ctas = sms * 6;
+    p->n_groups = std::max(1, std::min(p->M, (target_ctas + p->n_tiles_run - 1) / p->n_tiles_run));
     p->modes_per_group = (p->M + p->n_groups - 1) / p->n_groups;
     p->n_groups = (p->M + p->modes_per_group - 1) / p->modes_per_group;
     if (opt.cuda_stream) {
@@ -683,6 +720,8 @@ swkb_status swkb_plan_get_info(const swkb_plan* p, swkb_plan_info* info) {
   info->n_rays_total = p->NRT;
   info->tile_points = p->TM;
   info->mode_groups = p->n_groups;
+  info->march_modes = p->Mr;
+  info->resum_points = p->n_tiles_run * p->TM;
   info->dz = p->dz;
   info->period = p->L;
   info->eps_ref = p->eps_ref;

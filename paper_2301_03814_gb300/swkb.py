@@ -66,7 +66,8 @@ class swkb_options(ctypes.Structure):
 class swkb_plan_info(ctypes.Structure):
     _fields_ = [("n_fft", c_int32), ("n_max", c_int32), ("n_modes", c_int32),
                 ("n_rays", c_int32), ("n_ghost", c_int32), ("n_rays_total", c_int32),
-                ("tile_points", c_int32), ("mode_groups", c_int32), ("dz", c_double),
+                ("tile_points", c_int32), ("mode_groups", c_int32), ("march_modes", c_int32),
+                ("resum_points", c_int32), ("dz", c_double),
                 ("period", c_double), ("eps_ref", c_double), ("device_bytes", c_size_t)]
 
 

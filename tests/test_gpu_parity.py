@@ -84,6 +84,29 @@ def test_debug_screen_fp64_intermediates(q):
     assert rel_l2(got["u_next"], want_u) < FP64_TOL
 
 
+@pytest.mark.parametrize("prec,tol", [(swkb.SWKB_FP64, 1e-9), (swkb.SWKB_MIXED, 1e-4)])
+def test_debug_screen_grounded_mirrored_rays(prec, tol):
+    """Grounded plans march n >= 0 only; mode -n's rays are mirror images.
+    All modes' landings, phases and amplitudes still match the oracle's own
+    rays (ray 0 of a mirrored family has no partner and is NaN)."""
+    pb = duct_small()
+    o = Oracle(pb)
+    u = o.extend(pb.u0)
+    want_u, want_c, rays = o.screen(u, 3, keep_rays=True)
+    got = swkb.Plan(pb, prec).debug_screen(3, u)
+    delta = (rays["z"] - o.g.z_lo) / o.g.dz
+    neg = o.n < 0
+    assert np.all(np.isnan(got["delta"][neg, 0])) and not np.any(np.isnan(got["delta"][~neg]))
+    sl = (slice(None), slice(1, None))
+    # FP64: rounding only.  FP32: landings to 1e-3 grid cells (1.2e-6 m), phase
+    # to 1e-4 rad, amplitude factors to 1e-5.
+    tol_d, tol_phase, tol_a = (1e-9, 1e-8, 1e-10) if prec == swkb.SWKB_FP64 else (1e-3, 1e-4, 1e-5)
+    assert np.max(np.abs(got["delta"][sl] - delta[sl])) < tol_d
+    assert np.max(np.abs(got["r"][sl] - rays["r"][sl])) * pb.k < tol_phase
+    assert np.max(np.abs(got["a"][sl] - rays["a"][sl])) < tol_a
+    assert rel_l2(got["u_next"], o.project(want_u)) < tol
+
+
 def test_debug_screen_mixed_intermediates():
     pb = w.config_unit_periodic()
     o = Oracle(pb)
