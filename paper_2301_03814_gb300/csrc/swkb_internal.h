@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "swkb.h"
+
 namespace swkb {
 
 // Status bits written by device code (atomicOr) and mapped to swkb_status.
@@ -125,5 +127,21 @@ template <typename T> cudaError_t prepare_kernels(int resum_smem);
 void set_last_error(const char* msg);
 // Raise only the FFT kernel's shared-memory limit on the current device.
 template <typename T> cudaError_t prepare_fft_kernels();
+
+// Plan-level hooks used by the request server (swkb_server.cu).
+cudaStream_t plan_stream(swkb_plan* p);
+size_t plan_bytes(const swkb_plan* p);
+// Copy the n_z-point host field in and extend it to the period (async).
+swkb_status plan_begin(swkb_plan* p, const double* u0_host);
+// Enqueue screens q .. q + n - 1; first: the field was just set by plan_begin.
+swkb_status plan_advance(swkb_plan* p, int q, int n, bool first);
+// Enqueue the final reduction and the conversion to n_z complex128 (async).
+swkb_status plan_finish(swkb_plan* p, bool fresh);
+// Wait for the plan's stream, map its status, copy the result to the host.
+swkb_status plan_collect(swkb_plan* p, double* out_host);
+// Device bytes a plan with these arguments would hold (no allocation).
+swkb_status estimate_plan_bytes(const swkb_profile* prof, double k, const swkb_domain* dom,
+                                int32_t n_z, double screen_dx, const swkb_options* opt,
+                                size_t* bytes);
 
 }  // namespace swkb

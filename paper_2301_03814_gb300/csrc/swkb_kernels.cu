@@ -739,10 +739,19 @@ cudaError_t launch_resum(const ResumArgs<T>& a, cudaStream_t s) {
 
 template <typename T>
 cudaError_t prepare_kernels(int resum_smem) {
+  // The limit is a per-device property of the kernel shared by every plan in
+  // the process: raise it to the device's opt-in maximum (never lower it, or
+  // a plan with smaller tiles would break another plan's launches).
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  if (resum_smem > optin) return cudaErrorInvalidValue;
   const void* fs[] = {(const void*)k_resum<T, 2>, (const void*)k_resum<T, 4>,
                       (const void*)k_resum<T, 8>, (const void*)k_resum<T, 16>};
   for (const void* f : fs) {
-    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, resum_smem);
+    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

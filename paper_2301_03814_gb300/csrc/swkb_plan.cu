@@ -273,13 +273,13 @@ swkb_status build_device(swkb_plan* p, const swkb_profile* prof) {
   TRY(dev_alloc(p, &p->ra, rays * sizeof(T)));
   const size_t jn = (size_t)(p->n_tiles + 1) * p->Mr;
   TRY(dev_alloc(p, (void**)&p->jlo, jn * sizeof(int)));
-  CK(cudaMemset(p->jlo, 0, jn * sizeof(int)));
+  CK(cudaMemsetAsync(p->jlo, 0, jn * sizeof(int), p->stream));
   if (p->sym) {
     TRY(dev_alloc(p, (void**)&p->jlo_neg, jn * sizeof(int)));
-    CK(cudaMemset(p->jlo_neg, 0, jn * sizeof(int)));
+    CK(cudaMemsetAsync(p->jlo_neg, 0, jn * sizeof(int), p->stream));
   }
   TRY(dev_alloc(p, (void**)&p->status, sizeof(unsigned)));
-  CK(cudaMemset(p->status, 0, sizeof(unsigned)));
+  CK(cudaMemsetAsync(p->status, 0, sizeof(unsigned), p->stream));
   TRY(dev_alloc(p, (void**)&p->io, 2 * (size_t)std::max(N, p->n_z) * sizeof(double)));
   CK(prepare_kernels<T>((int)resum_smem_bytes<T>(p->wcap, p->TM)));
   return SWKB_OK;
@@ -565,131 +565,236 @@ const char* swkb_status_string(swkb_status s) {
   return "unknown status";
 }
 
+}  // extern "C"
+
+namespace {
+
+// Validate the arguments and derive every size of the plan (host only).
+swkb_status configure(swkb_plan* p, const swkb_profile* prof, double k, const swkb_domain* dom,
+                      int32_t n_z, double screen_dx, const swkb_options& opt) {
+  if (!prof || !dom) return fail(SWKB_ERR_INVALID_ARG, "profile or domain is NULL");
+  if (!(k > 0) || !std::isfinite(k)) return fail(SWKB_ERR_INVALID_ARG, "k must be > 0");
+  if (!(dom->z_b > dom->z_a)) return fail(SWKB_ERR_INVALID_ARG, "need z_b > z_a");
+  if (!(screen_dx > 0)) return fail(SWKB_ERR_INVALID_ARG, "screen spacing must be > 0");
+  if (dom->bc < SWKB_BC_PERIODIC || dom->bc > SWKB_BC_DIRICHLET)
+    return fail(SWKB_ERR_INVALID_ARG, "unknown boundary condition %d", dom->bc);
+  if (opt.precision != SWKB_FP64 && opt.precision != SWKB_MIXED)
+    return fail(SWKB_ERR_INVALID_ARG, "unknown precision %d", opt.precision);
+  if (prof->n_cols < 1 || prof->n_p < 3 || !(prof->dz_p > 0) || !prof->x_cols || !prof->eps ||
+      !prof->eps_z || !prof->eps_zz)
+    return fail(SWKB_ERR_INVALID_ARG, "malformed profile table");
+  for (int c = 1; c < prof->n_cols; ++c)
+    if (!(prof->x_cols[c] >= prof->x_cols[c - 1]))
+      return fail(SWKB_ERR_INVALID_ARG, "x_cols must be non-decreasing");
+  const size_t nt = (size_t)prof->n_cols * prof->n_p;
+  for (size_t i = 0; i < nt; ++i)
+    if (!std::isfinite(prof->eps[i]) || !std::isfinite(prof->eps_z[i]) ||
+        !std::isfinite(prof->eps_zz[i]))
+      return fail(SWKB_ERR_INVALID_ARG, "profile table has non-finite entries");
+  p->precision = opt.precision;
+  p->bc = dom->bc;
+  p->mirror = dom->bc == SWKB_BC_NEUMANN ? 1 : (dom->bc == SWKB_BC_DIRICHLET ? -1 : 0);
+  p->k = k; p->z_a = dom->z_a; p->z_b = dom->z_b; p->x0 = dom->x0; p->dx = screen_dx;
+  p->n_z = n_z;
+  const double H = dom->z_b - dom->z_a;
+  p->N = p->mirror ? 2 * n_z : n_z;
+  if (n_z < 1 || !is_pow2(p->N) || p->N < 64 || p->N > (1 << 20))
+    return fail(SWKB_ERR_INVALID_ARG, "FFT length %d must be a power of two in [64, 2^20]", p->N);
+  p->L = p->mirror ? 2 * H : H;
+  p->dz = H / n_z;
+  p->z_lo = p->mirror ? dom->z_a - H : dom->z_a;
+  const double lam = 2.0 * M_PI / k;
+  if (opt.n_max > 0) p->n_max = opt.n_max;
+  else p->n_max = (int)floor(sin(opt.theta_max) * p->L / lam * (1.0 + 1e-12));
+  p->n_max = std::min(p->n_max, p->N / 2 - 1);
+  if (p->n_max < 1) return fail(SWKB_ERR_INVALID_ARG, "no propagating mode kept (n_max < 1)");
+  p->M = 2 * p->n_max + 1;
+  p->R = opt.ray_stride;
+  if (p->R < 1 || p->N % p->R) return fail(SWKB_ERR_INVALID_ARG, "ray stride must divide N");
+  p->N_r = p->N / p->R;
+  p->Nt = opt.rk4_steps;
+  if (p->Nt < 1 || p->Nt > 4096) return fail(SWKB_ERR_INVALID_ARG, "rk4_steps out of range");
+  const double kmax = p->n_max * lam / p->L;
+  if (!(kmax < 1.0)) return fail(SWKB_ERR_INVALID_ARG, "kept modes reach grazing angle");
+  const double tan_t = kmax / sqrt(1.0 - kmax * kmax);
+  p->G = (int)ceil(screen_dx * tan_t / (p->R * p->dz) - 1e-9) + 3;
+  p->NRT = p->N_r + 2 * p->G;
+  p->absorber_frac = opt.absorber_frac;
+  if (!(p->absorber_frac >= 0 && p->absorber_frac < 1))
+    return fail(SWKB_ERR_INVALID_ARG, "absorber_frac must be in [0, 1)");
+  // DFT split N = N1 N2 with N1 ~ sqrt(M): pass 1 costs N N1, pass 2 M N2
+  p->N1 = 1;
+  while (p->N1 * p->N1 * 2 < p->M && p->N1 < p->N / 32 && p->N1 < 64) p->N1 *= 2;
+  p->N2 = p->N / p->N1;
+  p->log2N2 = ilog2(p->N2);
+  // medium
+  p->n_cols = prof->n_cols; p->n_p = prof->n_p; p->n_int = prof->n_p - 1;
+  p->z0p = prof->z0_p; p->dzp = prof->dz_p;
+  p->x_cols.assign(prof->x_cols, prof->x_cols + prof->n_cols);
+  const double ztop = p->z0p + p->dzp * (p->n_p - 1);
+  if (p->mirror) {
+    if (fabs(p->z0p - p->z_a) > 1e-9 * (1.0 + fabs(p->z_a)))
+      return fail(SWKB_ERR_INVALID_ARG, "grounded domains need the table to start at z_a");
+    double mx = 0;
+    for (size_t i = 0; i < nt; ++i) mx = std::max(mx, fabs(prof->eps_z[i]));
+    for (int c = 0; c < p->n_cols; ++c)
+      if (fabs(prof->eps_z[(size_t)c * p->n_p]) > 1e-12 * (1.0 + mx))
+        return fail(SWKB_ERR_INVALID_ARG, "grounded domains need eps_z = 0 at z_a");
+  }
+  {
+    const double reach = 1.5 * screen_dx * tan_t + 2.0 * p->dzp;
+    const double s_first = p->z_lo - (double)p->G * p->R * p->dz;
+    const double s_last = p->z_lo + (double)(p->NRT - 1 - p->G) * p->R * p->dz;
+    double lo = s_first - reach, hi = s_last + reach;
+    if (p->mirror) {
+      hi = p->z_a + std::max(fabs(lo - p->z_a), fabs(hi - p->z_a));
+      lo = p->z_a;
+    }
+    if (lo < p->z0p - 1e-9 || hi > ztop + 1e-9)
+      return fail(SWKB_ERR_INVALID_ARG,
+                  "permittivity table covers [%g, %g] but rays may reach [%g, %g]", p->z0p,
+                  ztop, lo, hi);
+  }
+  {
+    const double zm = 0.5 * (p->z_a + p->z_b);
+    long long im = llround((zm - p->z0p) / p->dzp);
+    im = std::min<long long>(std::max<long long>(im, 0), p->n_p - 1);
+    p->eps_ref = prof->eps[im];
+    if (!(p->eps_ref - kmax * kmax > 0))
+      return fail(SWKB_ERR_INVALID_ARG, "steepest kept mode is evanescent at eps_ref");
+  }
+  if (p->n_cols > 1) {
+    const double q_end = ceil((p->x_cols.back() - p->x0) / p->dx);
+    p->stage_rows = (int)std::min(std::max(q_end, 0.0), 1e6) + 1;
+  }
+  // grounded domains: mode -n is the mirror image of mode n and the field
+  // is even / odd, so only n >= 0 is marched and only z >= z_a summed
+  p->sym = p->mirror != 0;
+  p->Mr = p->sym ? p->n_max + 1 : p->M;
+  // resummation tiling
+  p->PW = p->R >= 8 ? 8 : (p->R >= 2 ? 4 : 2);
+  while (32 * p->PW > (p->sym ? p->N / 2 : p->N)) p->PW /= 2;
+  p->TM = 32 * p->PW;
+  p->n_tiles = p->N / p->TM;
+  p->n_tiles_run = p->sym ? p->n_tiles / 2 + 1 : p->n_tiles;
+  p->wcap = 4 * p->TM / p->R + 8;   // rays per tile window: up to 4x compression
+  p->device = opt.device;
+  CK(cudaSetDevice(p->device));
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
+  const int target_ctas = sms * 6;
+  p->n_groups = std::max(1, std::min(p->M, (target_ctas + p->n_tiles_run - 1) / p->n_tiles_run));
+  p->modes_per_group = (p->M + p->n_groups - 1) / p->n_groups;
+  p->n_groups = (p->M + p->modes_per_group - 1) / p->modes_per_group;
+  return SWKB_OK;
+}
+
+// Device bytes build_device will allocate for a configured plan.
+size_t device_bytes(const swkb_plan* p) {
+  const size_t T = p->precision == SWKB_FP64 ? 8 : 4, V = 2 * T;
+  const size_t S = 2 * (size_t)p->Nt + 1;
+  size_t b = (size_t)p->n_cols * p->n_int * 8 * T;                  // medium
+  b += (size_t)p->stage_rows * S * (sizeof(int) + T);               // stage columns
+  b += 3 * (size_t)p->M * T + (size_t)p->M * V;                     // mode tables
+  b += (size_t)p->N * V;                                            // twiddles
+  if (p->absorber_frac > 0) b += (size_t)p->N * T;                  // absorber
+  b += (size_t)p->N * V * (2 + (size_t)p->n_groups) + (size_t)p->M * V;  // u, Y, partials, c
+  b += 3 * (size_t)p->NRT * p->Mr * T;                              // rays
+  b += (size_t)(p->n_tiles + 1) * p->Mr * sizeof(int) * (p->sym ? 2 : 1);
+  b += 16 + 2 * (size_t)std::max(p->N, p->n_z) * sizeof(double);   // status, io
+  return b;
+}
+
+}  // namespace
+
+namespace {
+
+template <typename T>
+swkb_status begin_t(swkb_plan* p, const double* u0_host) {
+  using V = typename C2<T>::type;
+  CK(cudaMemcpyAsync(p->io, u0_host, 2 * sizeof(double) * p->n_z, cudaMemcpyHostToDevice,
+                     p->stream));
+  TRY(timed(p, SWKB_KERNEL_INIT, 1,
+            [&] { return launch_init<T>(p->io, p->n_z, p->N, p->mirror, (V*)p->u, p->stream); }));
+  return SWKB_OK;
+}
+
+template <typename T>
+swkb_status finish_t(swkb_plan* p, bool fresh) {
+  using V = typename C2<T>::type;
+  if (!fresh) TRY(reduce_to_u<T>(p, true));
+  const int off = p->mirror ? p->n_z : 0;
+  TRY(timed(p, SWKB_KERNEL_OUTPUT, 1,
+            [&] { return launch_output<T>((const V*)p->u, off, p->n_z, p->io, p->stream); }));
+  return SWKB_OK;
+}
+
+}  // namespace
+
+namespace swkb {
+
+cudaStream_t plan_stream(swkb_plan* p) { return p->stream; }
+size_t plan_bytes(const swkb_plan* p) { return p->bytes; }
+
+swkb_status plan_begin(swkb_plan* p, const double* u0_host) {
+  CK(cudaSetDevice(p->device));
+  return p->precision == SWKB_FP64 ? begin_t<double>(p, u0_host) : begin_t<float>(p, u0_host);
+}
+
+swkb_status plan_advance(swkb_plan* p, int q, int n, bool first) {
+  CK(cudaSetDevice(p->device));
+  for (int i = 0; i < n; ++i) {
+    const bool fresh = first && i == 0;
+    swkb_status st = p->precision == SWKB_FP64 ? launch_screen<double>(p, q + i, fresh)
+                                               : launch_screen<float>(p, q + i, fresh);
+    if (st != SWKB_OK) return st;
+  }
+  return SWKB_OK;
+}
+
+swkb_status plan_finish(swkb_plan* p, bool fresh) {
+  CK(cudaSetDevice(p->device));
+  return p->precision == SWKB_FP64 ? finish_t<double>(p, fresh) : finish_t<float>(p, fresh);
+}
+
+swkb_status plan_collect(swkb_plan* p, double* out_host) {
+  CK(cudaSetDevice(p->device));
+  swkb_status st = read_status(p);   // synchronises the plan's stream
+  if (st != SWKB_OK) return st;
+  CK(cudaMemcpy(out_host, p->io, 2 * sizeof(double) * p->n_z, cudaMemcpyDeviceToHost));
+  return SWKB_OK;
+}
+
+swkb_status estimate_plan_bytes(const swkb_profile* prof, double k, const swkb_domain* dom,
+                                int32_t n_z, double screen_dx, const swkb_options* opt_in,
+                                size_t* bytes) {
+  try {
+    swkb_options opt;
+    if (opt_in) opt = *opt_in; else swkb_options_default(&opt);
+    swkb_plan tmp;
+    TRY(configure(&tmp, prof, k, dom, n_z, screen_dx, opt));
+    *bytes = device_bytes(&tmp);
+    return SWKB_OK;
+  } catch (...) {
+    return fail(SWKB_ERR_INVALID_ARG, "unexpected exception");
+  }
+}
+
+}  // namespace swkb
+
+extern "C" {
+
 swkb_status swkb_plan_create(const swkb_profile* prof, double k, const swkb_domain* dom,
                              int32_t n_z, double screen_dx, const swkb_options* opt_in,
                              swkb_plan** out) {
   try {
     if (!out) return fail(SWKB_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
-    if (!prof || !dom) return fail(SWKB_ERR_INVALID_ARG, "profile or domain is NULL");
     swkb_options opt;
     if (opt_in) opt = *opt_in; else swkb_options_default(&opt);
-    if (!(k > 0) || !std::isfinite(k)) return fail(SWKB_ERR_INVALID_ARG, "k must be > 0");
-    if (!(dom->z_b > dom->z_a)) return fail(SWKB_ERR_INVALID_ARG, "need z_b > z_a");
-    if (!(screen_dx > 0)) return fail(SWKB_ERR_INVALID_ARG, "screen spacing must be > 0");
-    if (dom->bc < SWKB_BC_PERIODIC || dom->bc > SWKB_BC_DIRICHLET)
-      return fail(SWKB_ERR_INVALID_ARG, "unknown boundary condition %d", dom->bc);
-    if (opt.precision != SWKB_FP64 && opt.precision != SWKB_MIXED)
-      return fail(SWKB_ERR_INVALID_ARG, "unknown precision %d", opt.precision);
-    if (prof->n_cols < 1 || prof->n_p < 3 || !(prof->dz_p > 0) || !prof->x_cols || !prof->eps ||
-        !prof->eps_z || !prof->eps_zz)
-      return fail(SWKB_ERR_INVALID_ARG, "malformed profile table");
-    for (int c = 1; c < prof->n_cols; ++c)
-      if (!(prof->x_cols[c] >= prof->x_cols[c - 1]))
-        return fail(SWKB_ERR_INVALID_ARG, "x_cols must be non-decreasing");
-    const size_t nt = (size_t)prof->n_cols * prof->n_p;
-    for (size_t i = 0; i < nt; ++i)
-      if (!std::isfinite(prof->eps[i]) || !std::isfinite(prof->eps_z[i]) ||
-          !std::isfinite(prof->eps_zz[i]))
-        return fail(SWKB_ERR_INVALID_ARG, "profile table has non-finite entries");
-
     swkb_plan* p = new swkb_plan();
     struct Guard { swkb_plan*& p; ~Guard() { if (p) release(p); } } guard{p};
-    p->precision = opt.precision;
-    p->bc = dom->bc;
-    p->mirror = dom->bc == SWKB_BC_NEUMANN ? 1 : (dom->bc == SWKB_BC_DIRICHLET ? -1 : 0);
-    p->k = k; p->z_a = dom->z_a; p->z_b = dom->z_b; p->x0 = dom->x0; p->dx = screen_dx;
-    p->n_z = n_z;
-    const double H = dom->z_b - dom->z_a;
-    p->N = p->mirror ? 2 * n_z : n_z;
-    if (n_z < 1 || !is_pow2(p->N) || p->N < 64 || p->N > (1 << 20))
-      return fail(SWKB_ERR_INVALID_ARG, "FFT length %d must be a power of two in [64, 2^20]", p->N);
-    p->L = p->mirror ? 2 * H : H;
-    p->dz = H / n_z;
-    p->z_lo = p->mirror ? dom->z_a - H : dom->z_a;
-    const double lam = 2.0 * M_PI / k;
-    if (opt.n_max > 0) p->n_max = opt.n_max;
-    else p->n_max = (int)floor(sin(opt.theta_max) * p->L / lam * (1.0 + 1e-12));
-    p->n_max = std::min(p->n_max, p->N / 2 - 1);
-    if (p->n_max < 1) return fail(SWKB_ERR_INVALID_ARG, "no propagating mode kept (n_max < 1)");
-    p->M = 2 * p->n_max + 1;
-    p->R = opt.ray_stride;
-    if (p->R < 1 || p->N % p->R) return fail(SWKB_ERR_INVALID_ARG, "ray stride must divide N");
-    p->N_r = p->N / p->R;
-    p->Nt = opt.rk4_steps;
-    if (p->Nt < 1 || p->Nt > 4096) return fail(SWKB_ERR_INVALID_ARG, "rk4_steps out of range");
-    const double kmax = p->n_max * lam / p->L;
-    if (!(kmax < 1.0)) return fail(SWKB_ERR_INVALID_ARG, "kept modes reach grazing angle");
-    const double tan_t = kmax / sqrt(1.0 - kmax * kmax);
-    p->G = (int)ceil(screen_dx * tan_t / (p->R * p->dz) - 1e-9) + 3;
-    p->NRT = p->N_r + 2 * p->G;
-    p->absorber_frac = opt.absorber_frac;
-    if (!(p->absorber_frac >= 0 && p->absorber_frac < 1))
-      return fail(SWKB_ERR_INVALID_ARG, "absorber_frac must be in [0, 1)");
-    // DFT split N = N1 N2 with N1 ~ sqrt(M): pass 1 costs N N1, pass 2 M N2
-    p->N1 = 1;
-    while (p->N1 * p->N1 * 2 < p->M && p->N1 < p->N / 32 && p->N1 < 64) p->N1 *= 2;
-    p->N2 = p->N / p->N1;
-    p->log2N2 = ilog2(p->N2);
-    // medium
-    p->n_cols = prof->n_cols; p->n_p = prof->n_p; p->n_int = prof->n_p - 1;
-    p->z0p = prof->z0_p; p->dzp = prof->dz_p;
-    p->x_cols.assign(prof->x_cols, prof->x_cols + prof->n_cols);
-    const double ztop = p->z0p + p->dzp * (p->n_p - 1);
-    if (p->mirror) {
-      if (fabs(p->z0p - p->z_a) > 1e-9 * (1.0 + fabs(p->z_a)))
-        return fail(SWKB_ERR_INVALID_ARG, "grounded domains need the table to start at z_a");
-      double mx = 0;
-      for (size_t i = 0; i < nt; ++i) mx = std::max(mx, fabs(prof->eps_z[i]));
-      for (int c = 0; c < p->n_cols; ++c)
-        if (fabs(prof->eps_z[(size_t)c * p->n_p]) > 1e-12 * (1.0 + mx))
-          return fail(SWKB_ERR_INVALID_ARG, "grounded domains need eps_z = 0 at z_a");
-    }
-    {
-      const double reach = 1.5 * screen_dx * tan_t + 2.0 * p->dzp;
-      const double s_first = p->z_lo - (double)p->G * p->R * p->dz;
-      const double s_last = p->z_lo + (double)(p->NRT - 1 - p->G) * p->R * p->dz;
-      double lo = s_first - reach, hi = s_last + reach;
-      if (p->mirror) {
-        hi = p->z_a + std::max(fabs(lo - p->z_a), fabs(hi - p->z_a));
-        lo = p->z_a;
-      }
-      if (lo < p->z0p - 1e-9 || hi > ztop + 1e-9)
-        return fail(SWKB_ERR_INVALID_ARG,
-                    "permittivity table covers [%g, %g] but rays may reach [%g, %g]", p->z0p,
-                    ztop, lo, hi);
-    }
-    {
-      const double zm = 0.5 * (p->z_a + p->z_b);
-      long long im = llround((zm - p->z0p) / p->dzp);
-      im = std::min<long long>(std::max<long long>(im, 0), p->n_p - 1);
-      p->eps_ref = prof->eps[im];
-      if (!(p->eps_ref - kmax * kmax > 0))
-        return fail(SWKB_ERR_INVALID_ARG, "steepest kept mode is evanescent at eps_ref");
-    }
-    if (p->n_cols > 1) {
-      const double q_end = ceil((p->x_cols.back() - p->x0) / p->dx);
-      p->stage_rows = (int)std::min(std::max(q_end, 0.0), 1e6) + 1;
-    }
-    // grounded domains: mode -n is the mirror image of mode n and the field
-    // is even / odd, so only n >= 0 is marched and only z >= z_a summed
-    p->sym = p->mirror != 0;
-    p->Mr = p->sym ? p->n_max + 1 : p->M;
-    // resummation tiling
-    p->PW = p->R >= 8 ? 8 : (p->R >= 2 ? 4 : 2);
-    while (32 * p->PW > (p->sym ? p->N / 2 : p->N)) p->PW /= 2;
-    p->TM = 32 * p->PW;
-    p->n_tiles = p->N / p->TM;
-    p->n_tiles_run = p->sym ? p->n_tiles / 2 + 1 : p->n_tiles;
-    p->wcap = 4 * p->TM / p->R + 8;   // rays per tile window: up to 4x compression
-    p->device = opt.device;
-    CK(cudaSetDevice(p->device));
-    int sms = 0;
-    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
-    const int target_ctas = sms * 6;
-    p->n_groups = std::max(1, std::min(p->M, (target_ctas + p->n_tiles_run - 1) / p->n_tiles_run));
-    p->modes_per_group = (p->M + p->n_groups - 1) / p->n_groups;
-    p->n_groups = (p->M + p->modes_per_group - 1) / p->modes_per_group;
+    TRY(configure(p, prof, k, dom, n_z, screen_dx, opt));
     if (opt.cuda_stream) {
       p->stream = (cudaStream_t)opt.cuda_stream;
     } else {
@@ -699,7 +804,7 @@ swkb_status swkb_plan_create(const swkb_profile* prof, double k, const swkb_doma
     swkb_status st = p->precision == SWKB_FP64 ? build_device<double>(p, prof)
                                                : build_device<float>(p, prof);
     if (st != SWKB_OK) return st;
-    CK(cudaDeviceSynchronize());
+    CK(cudaStreamSynchronize(p->stream));
     *out = p;
     p = nullptr;  // disarm guard
     return SWKB_OK;

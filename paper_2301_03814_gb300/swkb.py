@@ -241,9 +241,89 @@ def swkb_last_error() -> str:
     return lib().swkb_last_error().decode(errors="replace")
 
 
+def swkb_server_create(hbm_budget_bytes, max_slots, queue_cap=0, device=0):
+    handle = c_void_p()
+    check(lib().swkb_server_create(int(hbm_budget_bytes), int(max_slots), int(queue_cap),
+                                   int(device), byref(handle)))
+    return handle
+
+
+def swkb_submit(server, req: swkb_request) -> tuple[int, int]:
+    """Returns (status, ticket); status SWKB_ERR_AGAIN when the queue is full."""
+    t = c_uint64()
+    st = lib().swkb_submit(server, byref(req), byref(t))
+    return st, int(t.value)
+
+
+def swkb_poll(server, ticket, u_out=None, timeout_ms=-1) -> int:
+    ptr = u_out.ctypes.data_as(c_void_p) if u_out is not None else None
+    return lib().swkb_poll(server, c_uint64(ticket), ptr, int(timeout_ms))
+
+
+def swkb_cancel(server, ticket) -> int:
+    return lib().swkb_cancel(server, c_uint64(ticket))
+
+
+def swkb_server_get_stats(server) -> dict:
+    st = swkb_server_stats()
+    check(lib().swkb_server_get_stats(server, byref(st)))
+    return {f: getattr(st, f) for f, _ in swkb_server_stats._fields_}
+
+
+def swkb_server_destroy(server):
+    lib().swkb_server_destroy(server)
+
+
 # --------------------------------------------------------------------------
-# convenience wrapper
+# convenience wrappers
 # --------------------------------------------------------------------------
+class Server:
+    """Continuous-batching request server (one GPU)."""
+
+    def __init__(self, hbm_budget_bytes, max_slots, queue_cap=0, device=0):
+        self.handle = swkb_server_create(hbm_budget_bytes, max_slots, queue_cap, device)
+        self.n_z = {}
+
+    def submit(self, problem, precision=SWKB_FP64, u0=None, q0=0, n_screens=None):
+        """Returns (status, ticket)."""
+        keep = _Keep()
+        prof = make_profile(problem.profile, keep)
+        dom = swkb_domain(problem.z_a, problem.z_b, problem.x0, problem.bc)
+        opt = options_for(problem, precision)
+        u = np.ascontiguousarray(problem.u0 if u0 is None else u0, dtype=np.complex128)
+        req = swkb_request(ctypes.pointer(prof), float(problem.k), ctypes.pointer(dom),
+                           int(problem.n_z), float(problem.dx), ctypes.pointer(opt),
+                           u.ctypes.data_as(POINTER(c_double)), int(q0),
+                           int(problem.n_screens if n_screens is None else n_screens))
+        st, t = swkb_submit(self.handle, req)
+        if st == SWKB_OK:
+            self.n_z[t] = problem.n_z
+        return st, t
+
+    def poll(self, ticket, timeout_ms=-1):
+        """Returns (status, field or None)."""
+        out = np.empty(self.n_z[ticket], np.complex128)
+        st = swkb_poll(self.handle, ticket, out, timeout_ms)
+        if st != SWKB_NOT_READY:
+            self.n_z.pop(ticket, None)
+        return st, (out if st == SWKB_OK else None)
+
+    def cancel(self, ticket):
+        return swkb_cancel(self.handle, ticket)
+
+    def stats(self):
+        return swkb_server_get_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            swkb_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 class Plan:
     """A plan for one workloads.Problem (or equivalent fields)."""
 

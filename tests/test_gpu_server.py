@@ -1,0 +1,149 @@
+"""Request server (continuous batching) on the GPU: results in the mix equal
+results alone; admission respects slots and the HBM budget; queue-full,
+cancellation and failing requests are reported through the ABI."""
+import math
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from paper_2301_03814_gb300 import swkb
+from paper_2301_03814_gb300 import workloads as w
+
+pytestmark = pytest.mark.gpu
+
+GB = 1 << 30
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def mix():
+    """Uneven requests: periodic unit-wavelength runs of different lengths, a
+    grounded duct in both precisions, a homogeneous Dirichlet case."""
+    return [
+        (w.config_unit_periodic(n_screens=10), swkb.SWKB_FP64),
+        (w.config_surface_duct_small(n_screens=6), swkb.SWKB_MIXED),
+        (w.config_unit_periodic(n_screens=3), swkb.SWKB_MIXED),
+        (w.config_surface_duct_small(n_screens=4), swkb.SWKB_FP64),
+        (w.config_homogeneous(bc=w.BC_DIRICHLET, ray_stride=2), swkb.SWKB_MIXED),
+        (w.config_unit_periodic(n_screens=7), swkb.SWKB_FP64),
+    ]
+
+
+def test_results_in_the_mix_equal_results_alone():
+    jobs = mix()
+    alone = [swkb.Plan(pb, prec).propagate() for pb, prec in jobs]
+    srv = swkb.Server(8 * GB, max_slots=3)
+    tickets = []
+    for pb, prec in jobs:
+        st, t = srv.submit(pb, prec)
+        assert st == swkb.SWKB_OK
+        tickets.append(t)
+    for t, want in zip(tickets, alone):
+        st, got = srv.poll(t, timeout_ms=120_000)
+        assert st == swkb.SWKB_OK, swkb.swkb_last_error()
+        assert np.array_equal(got, want)
+    s = srv.stats()
+    assert s["completed"] == len(jobs) and s["failed"] == 0 and s["resident"] == 0
+    srv.close()
+
+
+def test_arrivals_during_service_are_admitted():
+    """Continuous batching: requests submitted while another runs are admitted
+    next to it and their work overlaps; each result still equals the
+    request run alone."""
+    long_job = (w.config_surface_duct_small(n_screens=1500, seed=21), swkb.SWKB_MIXED)
+    late = [(w.config_surface_duct_small(n_screens=60, seed=s), swkb.SWKB_MIXED)
+            for s in (22, 23, 24)]
+    srv = swkb.Server(8 * GB, max_slots=4)
+    st, t0 = srv.submit(*long_job)
+    assert st == swkb.SWKB_OK
+    deadline = time.time() + 30
+    while srv.stats()["resident"] < 1 and time.time() < deadline:
+        time.sleep(0.001)
+    tickets = []
+    for pb, prec in late:
+        st, t = srv.submit(pb, prec)
+        assert st == swkb.SWKB_OK
+        tickets.append(t)
+    peak = 0
+    while srv.stats()["completed"] < len(late) and time.time() < deadline:
+        peak = max(peak, srv.stats()["resident"])
+        time.sleep(0.0005)
+    assert peak >= 2
+    for t, (pb, prec) in zip(tickets, late):
+        st, got = srv.poll(t, timeout_ms=120_000)
+        assert st == swkb.SWKB_OK
+        assert np.array_equal(got, swkb.Plan(pb, prec).propagate())
+    assert srv.poll(t0, timeout_ms=120_000)[0] == swkb.SWKB_OK
+    srv.close()
+
+
+def test_budget_limits_residency():
+    pb = w.config_surface_duct_small(n_screens=400)
+    one = swkb.Plan(pb, swkb.SWKB_MIXED).info.device_bytes
+    srv = swkb.Server(int(1.5 * one), max_slots=4)   # room for one request at a time
+    tickets = [srv.submit(pb, swkb.SWKB_MIXED)[1] for _ in range(3)]
+    peak = 0
+    while True:
+        s = srv.stats()
+        peak = max(peak, s["resident"])
+        assert s["hbm_in_use"] <= int(1.5 * one)
+        if s["completed"] + s["failed"] == 3:
+            break
+        time.sleep(0.001)
+    assert peak == 1                  # never two resident, though four slots are free
+    for t in tickets:
+        assert srv.poll(t, timeout_ms=60_000)[0] == swkb.SWKB_OK
+    srv.close()
+
+
+def test_queue_full_cancel_and_failures():
+    srv = swkb.Server(8 * GB, max_slots=1, queue_cap=2)
+    long_job = w.config_surface_duct_small(n_screens=400)
+    st, a = srv.submit(long_job, swkb.SWKB_FP64)
+    assert st == swkb.SWKB_OK
+    time.sleep(0.2)                   # a is admitted; the queue is empty again
+    st, b = srv.submit(long_job, swkb.SWKB_MIXED)
+    assert st == swkb.SWKB_OK
+    st, c = srv.submit(long_job, swkb.SWKB_MIXED)
+    assert st == swkb.SWKB_OK
+    st, _ = srv.submit(long_job, swkb.SWKB_MIXED)
+    assert st == swkb.SWKB_ERR_AGAIN  # queue (capacity 2) is full
+    assert srv.cancel(b) == swkb.SWKB_OK
+    assert srv.poll(b, timeout_ms=0)[0] == swkb.SWKB_ERR_CANCELLED
+    # a request that reaches a caustic fails once, with its status
+    caustic = w.config_gaussian_medium(a=0.05, b=0.01, dx=100.0, n_screens=1)
+    pr = caustic.profile
+    caustic = caustic.with_(profile=w._table([0.0], -160.0, pr.dz, int(384 / pr.dz) + 1,
+                                             [w.f_gaussian(0.05, 0.01, zc=32.0)]))
+    assert srv.poll(c, timeout_ms=120_000)[0] == swkb.SWKB_OK
+    st, d = srv.submit(caustic, swkb.SWKB_FP64)
+    assert st == swkb.SWKB_OK
+    assert srv.poll(d, timeout_ms=60_000)[0] == swkb.SWKB_ERR_CAUSTIC
+    assert swkb.swkb_poll(srv.handle, d, None, 0) == swkb.SWKB_ERR_INVALID_ARG   # ticket gone
+    assert srv.poll(a, timeout_ms=120_000)[0] == swkb.SWKB_OK
+    s = srv.stats()
+    assert s["rejected"] == 1 and s["failed"] == 2 and s["completed"] == 2
+    srv.close()
+
+
+def test_invalid_and_oversized_requests():
+    srv = swkb.Server(1 << 20, max_slots=1)        # 1 MiB: too small for the duct
+    k = 2 * math.pi
+    short = w._table([0.0], -2.0, 0.125, 540, [w.f_const(1.0)])
+    z = 64.0 / 256 * np.arange(256)
+    bad = w.Problem("short", k, 0.0, 64.0, 256, w.BC_PERIODIC, 0.0, 20.0, 1, short,
+                    w.gaussian_beam(z, k, 32, 3, 0.0), math.radians(30.0), 1, 8)
+    st, _ = srv.submit(bad)
+    assert st == swkb.SWKB_ERR_INVALID_ARG     # rejected at submission
+    st, t = srv.submit(w.config_surface_duct_small(n_screens=2), swkb.SWKB_MIXED)
+    assert st == swkb.SWKB_OK
+    assert srv.poll(t, timeout_ms=60_000)[0] == swkb.SWKB_ERR_OOM
+    srv.close()
