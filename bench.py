@@ -53,6 +53,7 @@ def parse_args():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     return ap.parse_args()
 
 
@@ -214,6 +215,81 @@ def kernel_traffic(kind):
         return None
 
 
+def serving_measurement(swkb, n_requests=48, rate_hz=20.0, seed=5, precision=None):
+    """Served stream: Poisson arrivals of uneven requests (drawn like the
+    batch instances, range 1-5 km, N_z 2^12..2^15), submitted through
+    swkb_submit at their arrival times; latency = arrival -> result ready."""
+    import threading
+    from paper_2301_03814_gb300 import workloads as w
+    rng = np.random.default_rng(seed)
+    reqs = [w.random_request(rng, n_z_range=(1 << 12, 1 << 15), range_km=(1.0, 5.0))
+            for _ in range(n_requests)]
+    gaps = rng.exponential(1.0 / rate_hz, n_requests)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    prec = swkb.SWKB_MIXED if precision is None else precision
+    srv = swkb.Server(64 << 30, max_slots=8)
+    t0 = time.perf_counter()
+    tickets = [None] * n_requests
+    done = [None] * n_requests
+    submitted = threading.Event()
+
+    def submitter():
+        for i, pb in enumerate(reqs):
+            while time.perf_counter() - t0 < arrivals[i]:
+                time.sleep(0.0002)
+            st, t = srv.submit(pb, prec)
+            tickets[i] = (st, t)
+        submitted.set()
+    th = threading.Thread(target=submitter)
+    th.start()
+    pending = set()
+    nxt = 0
+    statuses = []
+    while nxt < n_requests or pending:
+        while nxt < n_requests and tickets[nxt] is not None:
+            st, t = tickets[nxt]
+            if st == swkb.SWKB_OK:
+                pending.add((nxt, t))
+            else:
+                statuses.append(st)
+            nxt += 1
+        for (i, t) in list(pending):
+            st, _ = srv.poll(t, timeout_ms=0)
+            if st != swkb.SWKB_NOT_READY:
+                done[i] = time.perf_counter() - t0
+                statuses.append(st)
+                pending.discard((i, t))
+        time.sleep(0.0002)
+    th.join()
+    srv.close()
+    lat = np.array([done[i] - arrivals[i] for i in range(n_requests) if done[i] is not None]) * 1e3
+    pts = sum(pb.n_z * pb.n_screens for pb in reqs)
+    span = max(d for d in done if d is not None)
+    return {"requests": n_requests, "offered_rate_hz": rate_hz, "ok": int(sum(x == 0 for x in statuses)),
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "screen_points_per_s": pts / span, "wall_s": span,
+            "draw": "f U(1,10) GHz, H U(100,400) m, N_z 2^12..2^15, range U(1,5) km, "
+                    "20 screens/km, trilinear or evaporation duct, seed 5"}
+
+
+def batched_measurement(swkb, n=64, screens=10, seed=4):
+    """64 uneven instances (C4 draw, N_z 2^12..2^16), the first `screens`
+    screens of each, all submitted at once to the server (continuous
+    batching, up to 16 resident); whole-batch screen-points/s."""
+    from paper_2301_03814_gb300 import workloads as w
+    batch = [pb.with_(n_screens=min(pb.n_screens, screens)) for pb in w.batch_uneven(seed, n)]
+    srv = swkb.Server(96 << 30, max_slots=16)
+    t0 = time.perf_counter()
+    tickets = [srv.submit(pb, swkb.SWKB_MIXED)[1] for pb in batch]
+    sts = [srv.poll(t, timeout_ms=-1)[0] for t in tickets]
+    dt = time.perf_counter() - t0
+    srv.close()
+    pts = sum(pb.n_z * pb.n_screens for pb in batch)
+    return {"instances": n, "screens_each": screens, "ok": int(sum(x == 0 for x in sts)),
+            "screen_points_per_s": pts / dt, "wall_s": dt,
+            "draw": "C4: f U(1,10) GHz, H U(100,400) m, N_z 2^12..2^16, seed 4"}
+
+
 def run_ours(args, world, rank, local):
     import torch
     from paper_2301_03814_gb300 import swkb
@@ -335,6 +411,9 @@ def run_ours(args, world, rank, local):
             "kernel_share": share, "roofline": roofline, "clocks": clk,
             "step_ms": {"p50": statistics.median(ts), "p99": float(np.percentile(ts, 99)),
                         "min": min(ts), "max": max(ts)}}
+    if world == 1 and not args.no_serving:
+        line["serving"] = serving_measurement(swkb)
+        line["batched"] = batched_measurement(swkb)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(pb)
     print(json.dumps(line), flush=True)

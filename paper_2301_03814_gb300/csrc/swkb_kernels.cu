@@ -82,11 +82,11 @@ template <typename T>
 __device__ __forceinline__ void col_eval(const Medium<T>& m, int c, T zz, T& e, T& ez, T& ezz,
                                          unsigned& st) {
   const T u = (zz - m.z0) * m.inv_h;
-  // outside [0, n_int] (or NaN): flag and clamp to the nearest end interval
+  // outside [0, n_int] (or NaN): flag; the interval index is clamped in
+  // integers (a flagged ray's values are discarded, its reads stay in bounds)
   if (!(u >= T(0) && u <= T(m.n_int))) st |= ST_RANGE;
-  const T fi = fmin(fmax(floor(u), T(0)), T(m.n_int - 1));
-  const T t = fmin(fmax(u - fi, T(0)), T(1));
-  const int i = (int)fi;
+  const int i = min(max((int)floor(u), 0), m.n_int - 1);
+  const T t = u - T(i);
   T a0, a1, a2, a3, a4, a5;
   load6<T>(m.coef + (long long)c * m.col_stride + (long long)i * 8, a0, a1, a2, a3, a4, a5);
   // Horner with derivatives (synthetic division): p, p', p''/2 at t
@@ -214,6 +214,164 @@ __global__ void __launch_bounds__(256) k_march(const MarchArgs<T> p) {
   p.out_d[o] = y.dz * p.inv_dz;
   p.out_ph[o] = y.rh * p.k_over_2pi;
   p.out_a[o] = sqrt(P0 * rsqrt_t(P1sq) / Zs);
+  if (st) atomicOr(p.status, st);
+}
+
+// ----------------------------------------------------------------------------
+// (b) ray march, FP32 path with packed f32x2 arithmetic: each thread marches
+// two rays (j and j + 8 of one mode).  The medium lookups stay per ray; the
+// right-hand side of the ray + variational system and the RK4 updates run on
+// register pairs, halving their issue slots (same IEEE round-to-nearest
+// operations as the scalar kernel, in the same order up to FMA contraction).
+// ----------------------------------------------------------------------------
+struct f2 {
+  unsigned long long v;
+};
+__device__ __forceinline__ f2 mk2(float a, float b) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void sp2(f2 x, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x.v));
+}
+__device__ __forceinline__ f2 bc2(float a) { return mk2(a, a); }
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+  f2 r;
+  asm("add.rn.ftz.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+  f2 r;
+  asm("sub.rn.ftz.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+  f2 r;
+  asm("mul.rn.ftz.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {   // a b + c
+  f2 r;
+  asm("fma.rn.ftz.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+  return r;
+}
+
+struct Ray2 {
+  f2 dz, dQ, rh, Zs, Qs;
+};
+
+template <bool MULTI>
+__device__ __forceinline__ Ray2 rhs2(const MarchArgs<float>& p, int l, f2 s, f2 kap, f2 m2kap,
+                                     f2 mkap, f2 pb, f2 mpb, float pb2, f2 pb2v, const Ray2& y,
+                                     unsigned& st) {
+  float za, zb;
+  sp2(add2(s, y.dz), za, zb);
+  float ea, eza, ezza, eb, ezb, ezzb;
+  medium_eval<float, MULTI>(p, l, za, ea, eza, ezza, st);
+  medium_eval<float, MULTI>(p, l, zb, eb, ezb, ezzb, st);
+  const f2 e = mk2(ea, eb), ez = mk2(eza, ezb), ezz = mk2(ezza, ezzb);
+  const f2 Q = add2(kap, y.dQ);
+  const f2 D = fma2(y.dQ, sub2(m2kap, y.dQ), e);           // e - dQ (2 kappa + dQ)
+  float P2a, P2b;
+  sp2(add2(pb2v, D), P2a, P2b);
+  if (!(P2a > 0.f)) { st |= ST_TURNING; P2a = pb2; }
+  if (!(P2b > 0.f)) { st |= ST_TURNING; P2b = pb2; }
+  float Zsa, Zsb;
+  sp2(y.Zs, Zsa, Zsb);
+  if (!(Zsa > 0.f) || !(Zsb > 0.f)) st |= ST_CAUSTIC;
+  const float iPa = rsqrtf(P2a), iPb = rsqrtf(P2b);
+  const f2 iP = mk2(iPa, iPb);
+  const f2 P = mul2(mk2(P2a, P2b), iP);
+  const f2 hiP = mul2(bc2(0.5f), iP);
+  float da, db;
+  sp2(add2(pb, P), da, db);
+  const f2 rden = mk2(__fdividef(1.f, da), __fdividef(1.f, db));
+  Ray2 d;
+  d.dz = mul2(Q, iP);
+  d.dQ = mul2(ez, hiP);
+  // (e - kappa dQ - P_bar D / (P_bar + P)) / P
+  d.rh = mul2(fma2(mpb, mul2(D, rden), fma2(mkap, y.dQ, e)), iP);
+  // P_s / P = (eps_z Z_s - 2 Q Q_s) / (2 P^2)
+  const f2 PsiP = mul2(sub2(mul2(ez, y.Zs), mul2(add2(Q, Q), y.Qs)), mul2(hiP, iP));
+  d.Zs = mul2(sub2(y.Qs, mul2(Q, PsiP)), iP);
+  d.Qs = mul2(sub2(mul2(ezz, y.Zs), mul2(ez, PsiP)), hiP);
+  return d;
+}
+
+__device__ __forceinline__ Ray2 axpy2(const Ray2& y, f2 a, const Ray2& k) {
+  return Ray2{fma2(a, k.dz, y.dz), fma2(a, k.dQ, y.dQ), fma2(a, k.rh, y.rh), fma2(a, k.Zs, y.Zs),
+              fma2(a, k.Qs, y.Qs)};
+}
+
+__device__ __forceinline__ f2 rk4_sum(f2 y, f2 h6, f2 k1, f2 k2, f2 k3, f2 k4) {
+  const f2 two = bc2(2.f);
+  return fma2(h6, add2(fma2(two, k3, fma2(two, k2, k1)), k4), y);
+}
+
+template <bool MULTI>
+__global__ void __launch_bounds__(256) k_march_x2(const MarchArgs<float> p) {
+  const int r = blockIdx.x * 32 + threadIdx.x;
+  const int ja = blockIdx.y * 16 + threadIdx.y;
+  const int jb = ja + 8;
+  if (r >= p.Mr || ja >= p.NRT) return;
+  const bool has_b = jb < p.NRT;
+  unsigned st = 0;
+  const int i = r + p.mode_off;
+  const float kap = p.kappa[i], pb = p.pbar[i], pb2 = p.pbar2[i];
+  const float sa = p.z_lo + float((ja - p.G) * p.R) * p.dz;
+  const float sb = has_b ? p.z_lo + float((jb - p.G) * p.R) * p.dz : sa;
+  const f2 s = mk2(sa, sb), kv = bc2(kap), m2kap = bc2(-2.f * kap), mkap = bc2(-kap);
+  const f2 pbv = bc2(pb), mpb = bc2(-pb), pb2v = bc2(pb2);
+  float e0a, e0b, t0, t1;
+  medium_eval<float, MULTI>(p, 0, sa, e0a, t0, t1, st);
+  medium_eval<float, MULTI>(p, 0, sb, e0b, t0, t1, st);
+  float P0a = pb2 + e0a, P0b = pb2 + e0b;
+  if (!(P0a > 0.f)) { st |= ST_TURNING; P0a = pb2; }
+  if (!(P0b > 0.f)) { st |= ST_TURNING; P0b = pb2; }
+  P0a = sqrtf(P0a);
+  P0b = sqrtf(P0b);
+  const f2 zero = bc2(0.f);
+  Ray2 y{zero, zero, zero, bc2(1.f), zero};
+  const f2 h = bc2(p.h), hh = bc2(0.5f * p.h), h6 = bc2(p.h / 6.f);
+  for (int n = 0; n < p.Nt; ++n) {
+    const Ray2 k1 = rhs2<MULTI>(p, 2 * n, s, kv, m2kap, mkap, pbv, mpb, pb2, pb2v, y, st);
+    const Ray2 k2 = rhs2<MULTI>(p, 2 * n + 1, s, kv, m2kap, mkap, pbv, mpb, pb2, pb2v,
+                                axpy2(y, hh, k1), st);
+    const Ray2 k3 = rhs2<MULTI>(p, 2 * n + 1, s, kv, m2kap, mkap, pbv, mpb, pb2, pb2v,
+                                axpy2(y, hh, k2), st);
+    const Ray2 k4 = rhs2<MULTI>(p, 2 * n + 2, s, kv, m2kap, mkap, pbv, mpb, pb2, pb2v,
+                                axpy2(y, h, k3), st);
+    y.dz = rk4_sum(y.dz, h6, k1.dz, k2.dz, k3.dz, k4.dz);
+    y.dQ = rk4_sum(y.dQ, h6, k1.dQ, k2.dQ, k3.dQ, k4.dQ);
+    y.rh = rk4_sum(y.rh, h6, k1.rh, k2.rh, k3.rh, k4.rh);
+    y.Zs = rk4_sum(y.Zs, h6, k1.Zs, k2.Zs, k3.Zs, k4.Zs);
+    y.Qs = rk4_sum(y.Qs, h6, k1.Qs, k2.Qs, k3.Qs, k4.Qs);
+  }
+  float dza, dzb, dQa, dQb, rha, rhb, Zsa, Zsb;
+  sp2(y.dz, dza, dzb);
+  sp2(y.dQ, dQa, dQb);
+  sp2(y.rh, rha, rhb);
+  sp2(y.Zs, Zsa, Zsb);
+  if (!(Zsa > 0.f) || !(Zsb > 0.f)) st |= ST_CAUSTIC;
+  float e1a, e1b;
+  medium_eval<float, MULTI>(p, 2 * p.Nt, sa + dza, e1a, t0, t1, st);
+  medium_eval<float, MULTI>(p, 2 * p.Nt, sb + dzb, e1b, t0, t1, st);
+  float P1a = pb2 + e1a - dQa * (2.f * kap + dQa);
+  float P1b = pb2 + e1b - dQb * (2.f * kap + dQb);
+  if (!(P1a > 0.f)) { st |= ST_TURNING; P1a = pb2; }
+  if (!(P1b > 0.f)) { st |= ST_TURNING; P1b = pb2; }
+  const float Za = Zsa > 0.f ? Zsa : 1.f, Zb = Zsb > 0.f ? Zsb : 1.f;
+  const long long oa = (long long)ja * p.Mr + r;
+  p.out_d[oa] = dza * p.inv_dz;
+  p.out_ph[oa] = rha * p.k_over_2pi;
+  p.out_a[oa] = sqrtf(P0a * rsqrtf(P1a) / Za);
+  if (has_b) {
+    const long long ob = (long long)jb * p.Mr + r;
+    p.out_d[ob] = dzb * p.inv_dz;
+    p.out_ph[ob] = rhb * p.k_over_2pi;
+    p.out_a[ob] = sqrtf(P0b * rsqrtf(P1b) / Zb);
+  }
   if (st) atomicOr(p.status, st);
 }
 
@@ -591,7 +749,7 @@ __device__ __forceinline__ typename C2<T>::type cmul(typename C2<T>::type a,
 // pass 1: a CTA takes 32 consecutive columns n2 (all N1 rows, one coalesced
 // tile in shared memory) and forms Y[k1][n2] = w_N^{n2 k1} sum_n1 x[n1 N2 + n2]
 // w_{N1}^{n1 k1} for all k1.  N1 <= 64.
-constexpr int FFT1_COLS = 32;
+constexpr int FFT1_COLS = 8;
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_fft1(const FftArgs<T> p) {
@@ -619,13 +777,9 @@ __global__ void __launch_bounds__(256) k_fft1(const FftArgs<T> p) {
   }
 }
 
-// w_{N2}^{idx}: FP32 computes it (sincospi, ~1 ulp), FP64 reads the table.
-__device__ __forceinline__ float2 twiddle2(const float2*, unsigned idx, int lgN2, int) {
-  float s, c;
-  sincospif(scalbnf((float)idx, 1 - lgN2), &s, &c);   // 2 idx / N2, exact
-  return make_float2(c, -s);
-}
-__device__ __forceinline__ double2 twiddle2(const double2* tw, unsigned idx, int, int N1) {
+// w_{N2}^{idx} from the table of w_N (w_{N2} = w_N^{N1}).
+template <typename V>
+__device__ __forceinline__ V twiddle2(const V* tw, unsigned idx, int, int N1) {
   return tw[(long long)idx * N1];
 }
 
@@ -704,6 +858,15 @@ cudaError_t launch_march(const MarchArgs<T>& a, bool multi_column, cudaStream_t 
   dim3 grid((a.Mr + 31) / 32, (a.NRT + 7) / 8);
   if (multi_column) k_march<T, true><<<grid, block, 0, s>>>(a);
   else k_march<T, false><<<grid, block, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_march<float>(const MarchArgs<float>& a, bool multi_column, cudaStream_t s) {
+  dim3 block(32, 8);
+  dim3 grid((a.Mr + 31) / 32, (a.NRT + 15) / 16);
+  if (multi_column) k_march_x2<true><<<grid, block, 0, s>>>(a);
+  else k_march_x2<false><<<grid, block, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -189,6 +189,34 @@ def f_trilinear_duct(z_t, g_d, M0=330.0, g_std=0.118, w=1.0, wg=1.0):
     return f
 
 
+def f_evaporation_duct(delta, M0=330.0, c1=0.125, z_rough=1.5e-4, zg=0.5):
+    """Evaporation duct of height delta (log-linear M profile with roughness
+    z_rough), continued below zg by the even quartic matching M, M', M'' there
+    so that the reflected profile is C^2 at the ground."""
+    def Mfun(z):
+        zz = np.maximum(z, zg)
+        M = M0 + c1 * zz - c1 * delta * np.log((zz + z_rough) / z_rough)
+        Mp = c1 - c1 * delta / (zz + z_rough)
+        Mpp = c1 * delta / (zz + z_rough) ** 2
+        return M, Mp, Mpp
+
+    Mw, Mpw, Mppw = (v[0] for v in Mfun(np.array([zg])))
+    c4 = (Mppw - Mpw / zg) / (8.0 * zg * zg)
+    c2 = (Mpw / zg - 4.0 * c4 * zg * zg) / 2.0
+    c0 = Mw - c2 * zg ** 2 - c4 * zg ** 4
+
+    def f(z):
+        M, Mp, Mpp = Mfun(z)
+        low = np.abs(z) < zg
+        zl = z[low]
+        M = M.copy(); Mp = Mp.copy(); Mpp = Mpp.copy()
+        M[low] = c0 + c2 * zl ** 2 + c4 * zl ** 4
+        Mp[low] = 2.0 * c2 * zl + 4.0 * c4 * zl ** 3
+        Mpp[low] = 2.0 * c2 + 12.0 * c4 * zl ** 2
+        return eps_from_M(M, Mp, Mpp)
+    return f
+
+
 # ----------------------------------------------------------------------------
 # incident fields
 # ----------------------------------------------------------------------------
@@ -327,6 +355,53 @@ def config_range_dependent_duct(seed=3, height=500.0, n_z=131072, range_m=100_00
     return Problem(f"range-dependent-duct-{n_z}", k, 0.0, height, n_z, BC_NEUMANN, 0.0, dx,
                    n_screens, prof, u0, math.radians(theta_max_deg), ray_stride, rk4_steps,
                    0.2, meta={"z_t0": z_t0, "g_d": g_d, "sign": sgn, "seed": seed})
+
+
+def random_request(rng, n_z_range=(1 << 12, 1 << 16), range_km=(5.0, 50.0), screens_per_km=20,
+                   dzp=0.05):
+    """One instance of the uneven batch / served stream: frequency U(1, 10)
+    GHz, height U(100, 400) m, N_z = 2^ceil(log2(4 H / lambda)) clamped to
+    n_z_range, range U(range_km) at screens_per_km, trilinear or evaporation
+    duct (coin flip; duct top U(20, 60) m and gradient U(-0.2, -0.05) M/m, or
+    evaporation height U(5, 40) m), Gaussian antenna of beamwidth U(0.5, 2) deg
+    at U(5, 30) m, theta_max = 3 beamwidths + 0.5 deg, one ray per R grid
+    points with R the power of two nearest 0.25 m / dz, 16 RK4 steps."""
+    f_hz = float(rng.uniform(1e9, 10e9))
+    lam = 299_792_458.0 / f_hz
+    H = float(rng.uniform(100.0, 400.0))
+    n_z = int(2 ** math.ceil(math.log2(4.0 * H / lam)))
+    n_z = int(min(max(n_z, n_z_range[0]), n_z_range[1]))
+    rng_m = float(rng.uniform(*range_km)) * 1000.0
+    n_screens = max(1, int(round(rng_m / 1000.0 * screens_per_km)))
+    dx = 1000.0 / screens_per_km
+    bw = float(rng.uniform(0.5, 2.0))
+    z_s = float(rng.uniform(5.0, 30.0))
+    theta_max = math.radians(3.0 * bw + 0.5)
+    dz = H / n_z
+    R = int(2 ** round(math.log2(max(0.25 / dz, 1.0))))
+    k = 2.0 * math.pi / lam
+    if rng.uniform() < 0.5:
+        prof_f = f_trilinear_duct(float(rng.uniform(20.0, 60.0)), float(rng.uniform(-0.2, -0.05)))
+        kind = "trilinear"
+    else:
+        prof_f = f_evaporation_duct(float(rng.uniform(5.0, 40.0)))
+        kind = "evaporation"
+    top = H + 2.0 * dx * math.tan(theta_max) + 8.0 + 2 * R * dz * (
+        math.ceil(dx * math.tan(theta_max) / (R * dz)) + 4)
+    n_p = int(math.ceil(top / dzp)) + 1
+    prof = _table([0.0], 0.0, dzp, n_p, [prof_f])
+    z = H / n_z * np.arange(n_z)
+    u0 = antenna_beam(z, k, z_s, math.radians(bw), BC_NEUMANN)
+    return Problem(f"request-{kind}-{n_z}", k, 0.0, H, n_z, BC_NEUMANN, 0.0, dx, n_screens,
+                   prof, u0, theta_max, R, 16, 0.2,
+                   meta={"f_hz": f_hz, "range_m": n_screens * dx, "profile": kind,
+                         "beamwidth_deg": bw, "z_s": z_s})
+
+
+def batch_uneven(seed=4, n=64, **kw):
+    """64 uneven instances (frequency, height, N_z, range, duct profile)."""
+    rng = np.random.default_rng(seed)
+    return [random_request(rng, **kw) for _ in range(n)]
 
 
 WORKLOADS = {
