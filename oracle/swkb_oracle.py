@@ -406,6 +406,59 @@ class Oracle:
             return out, c, rays
         return out
 
+    def screen_points(self, u: np.ndarray, q: int, ms) -> np.ndarray:
+        """The modal sum of screen q (times the absorber, before the
+        reflection step) at the grid points ms only.  Same arithmetic as
+        screen(): for each point only the rays that can land near it are
+        marched, and the bracket found in that window is checked to have the
+        whole stencil inside it (a landing order that would differ from the
+        full ray family is an error, never silently used)."""
+        g = self.g
+        pb = self.pb
+        u = self.project(u)
+        c = self.modes(u)
+        s_all = self.launch_points()
+        kmax = g.n_max * (2.0 * math.pi / pb.k) / g.L
+        reach = pb.dx * kmax / math.sqrt(1.0 - kmax * kmax)
+        out = np.zeros(len(ms), dtype=np.complex128)
+        for idx, m in enumerate(ms):
+            zm = g.z_lo + g.dz * m
+            half = int(math.ceil((2.0 * reach + 4 * g.R * g.dz) / (g.R * g.dz))) + 4
+            while True:
+                jc = int(np.searchsorted(s_all, zm))
+                j0 = max(jc - half, 0)
+                j1 = min(jc + half, g.NRT - 1)
+                rays = self.march(q, self.kappa[:, None], s_all[None, j0:j1 + 1])
+                delta = (rays["z"] - g.z_lo) / g.dz
+                if np.any(np.diff(delta, axis=1) <= 0):
+                    raise CausticError("ray landings not increasing (rays crossed)")
+                jj = np.array([np.searchsorted(row, m, side="right") - 1 for row in delta])
+                if jj.min() >= 1 and jj.max() <= delta.shape[1] - 3:
+                    break
+                if j0 == 0 and j1 == g.NRT - 1:
+                    raise RangeError("ghost rays do not cover the screen")
+                half *= 2
+            acc = 0j
+            for i in range(len(self.n)):
+                j = jj[i]
+                x = [delta[i, j + o] for o in (-1, 0, 1, 2)]
+                vals = []
+                for v in (rays["r"][i], rays["a"][i]):
+                    f = [v[j + o] for o in (-1, 0, 1, 2)]
+                    tot = 0.0
+                    for p_ in range(4):
+                        wgt = 1.0
+                        for l_ in range(4):
+                            if l_ != p_:
+                                wgt *= (m - x[l_]) / (x[p_] - x[l_])
+                        tot += wgt * f[p_]
+                    vals.append(tot)
+                n = int(self.n[i])
+                base = 2.0 * math.pi * ((n * m) % g.N) / g.N
+                acc += c[i] * vals[1] * np.exp(1j * (base + pb.k * vals[0]))
+            out[idx] = acc * self.W[m]
+        return out
+
     def propagate(self, u_phys: np.ndarray, q0: int = 0, n_screens: int | None = None,
                   snapshots: bool = False):
         """Screens q0 .. q0+n_screens-1 from the physical field on Gamma_{q0};

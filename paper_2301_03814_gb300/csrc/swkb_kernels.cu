@@ -783,16 +783,19 @@ __device__ __forceinline__ V twiddle2(const V* tw, unsigned idx, int, int N1) {
   return tw[(long long)idx * N1];
 }
 
-// pass 2: one warp per kept mode n: X[k1 + N1 k2] = sum_n2 Y[k1][n2] w_{N2}^{n2 k2}
-// (direct, pruned: only the 2 n_max + 1 kept bins are formed); c_n = X / N
-// times the range-phase carry.
+// pass 2: one CTA (4 warps) per kept mode n:
+// X[k1 + N1 k2] = sum_n2 Y[k1][n2] w_{N2}^{n2 k2} (direct, pruned: only the
+// 2 n_max + 1 kept bins are formed); c_n = X / N times the range-phase carry.
+constexpr int FFT2_THREADS = 128;
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_fft2(const FftArgs<T> p) {
+__global__ void __launch_bounds__(FFT2_THREADS) k_fft2(const FftArgs<T> p) {
   using V = typename C2<T>::type;
+  __shared__ V wsum[FFT2_THREADS / 32];
   const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
   // grounded fields are even / odd, so c_{-n} = +-c_n: only n >= 0 is formed
-  const int i = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) + (p.mirror ? p.n_max : 0);
-  if (i > 2 * p.n_max) return;
+  const int i = blockIdx.x + (p.mirror ? p.n_max : 0);
   const int n = i - p.n_max;
   const int b = n >= 0 ? n : n + p.N;
   const int k1 = b & (p.N1 - 1);
@@ -800,7 +803,7 @@ __global__ void __launch_bounds__(256) k_fft2(const FftArgs<T> p) {
   const V* row = (p.N1 > 1 ? p.Y : p.u) + (long long)k1 * p.N2;
   V acc;
   acc.x = T(0); acc.y = T(0);
-  for (int n2 = lane; n2 < p.N2; n2 += 32) {
+  for (int n2 = threadIdx.x; n2 < p.N2; n2 += FFT2_THREADS) {
     const unsigned e = (unsigned)(((long long)n2 * k2) & (p.N2 - 1));
     const V t = cmul<T>(row[n2], twiddle2(p.tw, e, p.log2N2, p.N1));
     acc.x += t.x; acc.y += t.y;
@@ -810,9 +813,14 @@ __global__ void __launch_bounds__(256) k_fft2(const FftArgs<T> p) {
     acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
     acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
   }
-  if (lane == 0) {
-    acc.x *= p.inv_N; acc.y *= p.inv_N;
-    const V cv = cmul<T>(acc, p.ephi[i]);
+  if (lane == 0) wsum[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    V tot = wsum[0];
+#pragma unroll
+    for (int w = 1; w < FFT2_THREADS / 32; ++w) { tot.x += wsum[w].x; tot.y += wsum[w].y; }
+    tot.x *= p.inv_N; tot.y *= p.inv_N;
+    const V cv = cmul<T>(tot, p.ephi[i]);
     p.c[i] = cv;
     if (p.mirror && n > 0) {
       V cm;
@@ -847,8 +855,8 @@ cudaError_t launch_fft(const FftArgs<T>& a, cudaStream_t s) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  const int warps = a.mirror ? a.n_max + 1 : 2 * a.n_max + 1;
-  k_fft2<T><<<(warps + 7) / 8, 256, 0, s>>>(a);
+  const int modes = a.mirror ? a.n_max + 1 : 2 * a.n_max + 1;
+  k_fft2<T><<<modes, FFT2_THREADS, 0, s>>>(a);
   return cudaGetLastError();
 }
 

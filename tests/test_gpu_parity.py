@@ -242,3 +242,28 @@ def test_full_size_duct_mixed_vs_fp64_200_screens():
     b = swkb.Plan(pb, swkb.SWKB_MIXED).propagate()
     assert np.all(np.isfinite(a)) and np.linalg.norm(a) > 0.1 * np.linalg.norm(pb.u0)
     assert rel_l2(b, a) < MIXED_TOL
+
+
+def test_paper_scale_one_screen_sampled_vs_oracle():
+    """Paper-scale duct (N_z = 131072, 1395 modes, range-dependent profile
+    with 101 columns): one screen mid-range through the same plan shape as
+    the full 2000-screen run, compared with the oracle at sampled points."""
+    pb = w.config_range_dependent_duct()
+    o = Oracle(pb)
+    u = o.extend(pb.u0)
+    nz = pb.n_z
+    dz = (pb.z_b - pb.z_a) / nz
+    # across the 0.5 deg beam at 25 m, plus the ground and the upper air
+    ms = [nz + int(round(z / dz)) for z in (23.1, 24.37, 25.0, 25.52, 26.9, 0.0, 140.0)]
+    want = o.screen_points(u, 1000, ms)
+    for prec, tol in ((swkb.SWKB_FP64, FP64_TOL), (swkb.SWKB_MIXED, MIXED_TOL)):
+        got = swkb.Plan(pb, prec).propagate(q0=1000, n_screens=1)
+        scale = np.max(np.abs(got))
+        assert np.max(np.abs(got[np.array(ms) - nz] - want)) < tol * scale
+
+
+def test_paper_scale_mixed_vs_fp64_first_screens():
+    pb = w.config_range_dependent_duct()
+    a = swkb.Plan(pb).propagate(n_screens=20)
+    b = swkb.Plan(pb, swkb.SWKB_MIXED).propagate(n_screens=20)
+    assert rel_l2(b, a) < MIXED_TOL

@@ -127,3 +127,15 @@ def test_table_range_is_an_error():
                    w.gaussian_beam(z, k, 32, 3, 0.0), math.radians(30.0), 1, 8)
     with pytest.raises(RangeError):
         Oracle(pb).propagate(pb.u0)
+
+
+def test_sampled_screen_equals_full_screen():
+    """screen_points (rays marched in a window per point) reproduces the full
+    screen at sampled points, including points near the domain edges."""
+    pb = w.config_surface_duct_small(n_screens=1)
+    o = Oracle(pb)
+    u = o.extend(pb.u0)
+    full = o.screen(u, 2)
+    ms = [o.g.N // 2, o.g.N // 2 + 7, o.g.N - 40, 3 * o.g.N // 4 + 123, 100]
+    got = o.screen_points(u, 2, ms)
+    assert np.max(np.abs(got - full[ms])) < 1e-12 * np.max(np.abs(full))
