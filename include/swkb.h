@@ -105,7 +105,10 @@ typedef struct {
   int32_t rk4_steps;      /* N_t: RK4 steps per screen                        */
   double absorber_frac;   /* top absorber over this fraction of the height
                              (grounded domains only; 0 = off)                  */
-  int32_t autotune;       /* 1: time candidate tilings at plan creation       */
+  int32_t autotune;       /* 1: at plan creation, time the candidate launch
+                             shapes (resummation tile and CTAs per SM, DFT
+                             split) on the plan's buffers and keep the
+                             fastest; cached per shape for the process       */
   void* cuda_stream;      /* cudaStream_t to run on; NULL = a library stream  */
   int32_t device;         /* CUDA device ordinal                              */
 } swkb_options;
@@ -122,6 +125,7 @@ typedef struct {
                              n >= 0 only -- mode -n is the mirror image)      */
   int32_t resum_points;   /* grid points summed per screen (grounded domains:
                              the physical half plus one tile)                 */
+  int32_t fft_n1;         /* DFT split N = fft_n1 * (N / fft_n1)              */
   double dz, period;      /* grid spacing, period length                      */
   double eps_ref;         /* reference permittivity of the phase carry        */
   size_t device_bytes;    /* device memory held by the plan                   */
@@ -201,10 +205,12 @@ typedef struct {
                                                 while timing is on)            */
 } swkb_plan_stats;
 
-/* on = 1: record CUDA events around every kernel launch of this plan (on its
-   stream) and accumulate per-kind device time; on = 0: stop.  Both reset the
-   counters. */
-swkb_status swkb_plan_set_timing(swkb_plan* plan, int32_t on);
+/* kinds: bit mask of kernel kinds (1 << SWKB_KERNEL_*; SWKB_TIME_ALL for
+   every kind, 0 to stop) whose launches get CUDA events recorded around them
+   on the plan's stream, accumulating per-kind device time.  Resets the
+   counters.  Each timed launch adds two event records to the stream. */
+#define SWKB_TIME_ALL ((1 << SWKB_KERNEL_KINDS) - 1)
+swkb_status swkb_plan_set_timing(swkb_plan* plan, int32_t kinds);
 swkb_status swkb_plan_get_stats(const swkb_plan* plan, swkb_plan_stats* stats);
 
 /*

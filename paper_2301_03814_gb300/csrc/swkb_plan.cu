@@ -18,6 +18,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -74,11 +76,14 @@ struct swkb_plan {
   double eps_ref = 0, absorber_frac = 0;
   // resummation tiling
   int PW = 8, TM = 256, n_tiles = 0, n_groups = 1, modes_per_group = 1, wcap = 0;
+  int ctas_per_sm = 6, sms = 1;
+  int alloc_groups = 0, alloc_tiles = 0;   // buffer sizes: max over tuning candidates
   // medium
   int n_cols = 0, n_p = 0, n_int = 0;
   double z0p = 0, dzp = 0;
   std::vector<double> x_cols;
   int stage_rows = 1;  // screens q >= stage_rows - 1 share the last row
+  bool autotune = false;
   std::vector<double> pbar;  // host copy of P_bar_n (FP64)
   std::vector<double> ephi;  // exp(i k dx P_bar_n), interleaved
   // device
@@ -109,10 +114,21 @@ struct swkb_plan {
   std::vector<void*> allocs;
   // accounting
   swkb_plan_stats stats{};
-  bool timing = false;
+  unsigned timing = 0;               // bit k: time kernel kind k with CUDA events
   std::vector<cudaEvent_t> events;   // pool, reused every run
   struct Mark { int kind; int e0, e1; };
   std::vector<Mark> marks;           // pending, harvested after a sync
+  // captured propagations, replayed with cudaGraphLaunch
+  struct Graph {
+    int q0, n, snap, timing;
+    const double* in;
+    double* out;
+    cudaGraphExec_t exec;
+    std::vector<Mark> marks;         // event pairs the graph records
+    swkb_plan_stats delta;           // launches / screens one replay adds
+  };
+  std::vector<Graph> graphs;
+  bool use_graphs = true;
 };
 
 namespace {
@@ -264,14 +280,14 @@ swkb_status build_device(swkb_plan* p, const swkb_profile* prof) {
   }
   // work buffers
   TRY(dev_alloc(p, &p->u, (size_t)N * sizeof(V)));
-  TRY(dev_alloc(p, &p->part, (size_t)p->n_groups * N * sizeof(V)));
+  TRY(dev_alloc(p, &p->part, (size_t)p->alloc_groups * N * sizeof(V)));
   TRY(dev_alloc(p, &p->Y, (size_t)N * sizeof(V)));
   TRY(dev_alloc(p, &p->c, (size_t)M * sizeof(V)));
   const size_t rays = (size_t)p->NRT * p->Mr;
   TRY(dev_alloc(p, &p->rd, rays * sizeof(T)));
   TRY(dev_alloc(p, &p->rph, rays * sizeof(T)));
   TRY(dev_alloc(p, &p->ra, rays * sizeof(T)));
-  const size_t jn = (size_t)(p->n_tiles + 1) * p->Mr;
+  const size_t jn = (size_t)(p->alloc_tiles + 1) * p->Mr;
   TRY(dev_alloc(p, (void**)&p->jlo, jn * sizeof(int)));
   CK(cudaMemsetAsync(p->jlo, 0, jn * sizeof(int), p->stream));
   if (p->sym) {
@@ -300,15 +316,18 @@ swkb_status event_at(swkb_plan* p, int idx) {
 template <typename F>
 swkb_status timed(swkb_plan* p, int kind, int n_launches, F&& launch) {
   int e0 = -1, e1 = -1;
-  if (p->timing) {
+  const bool on = (p->timing >> kind) & 1u;
+  if (on) {
     e0 = 2 * (int)p->marks.size();
     e1 = e0 + 1;
     TRY(event_at(p, e1));
-    CK(cudaEventRecord(p->events[e0], p->stream));
+    // "external" records become event-record nodes when the stream is being
+    // captured into a graph (and are plain records otherwise)
+    CK(cudaEventRecordWithFlags(p->events[e0], p->stream, cudaEventRecordExternal));
   }
   CK(launch());
-  if (p->timing) {
-    CK(cudaEventRecord(p->events[e1], p->stream));
+  if (on) {
+    CK(cudaEventRecordWithFlags(p->events[e1], p->stream, cudaEventRecordExternal));
     p->marks.push_back({kind, e0, e1});
   }
   p->stats.launches += n_launches;
@@ -416,12 +435,13 @@ swkb_status read_status(swkb_plan* p) {
   return status_from_bits(bits);
 }
 
-// Screens q0 .. q0 + n - 1 from the n_z-point field u0 (device, complex128).
-// Each output field (the last one, or every snap-th) goes either to out_dev
-// + k n_z (device) or through the staging buffer to out_host + k n_z (host).
+// Enqueue screens q0 .. q0 + n - 1 from the n_z-point field u0 (device,
+// complex128).  Each output field (the last one, or every snap-th) goes
+// either to out_dev + k n_z (device) or through the staging buffer to
+// out_host + k n_z (host).
 template <typename T>
-swkb_status run(swkb_plan* p, const double* u0, int q0, int n, double* out_dev, double* out_host,
-                int snap) {
+swkb_status enqueue(swkb_plan* p, const double* u0, int q0, int n, double* out_dev,
+                    double* out_host, int snap) {
   using V = typename C2<T>::type;
   const int off = p->mirror ? p->n_z : 0;
   const size_t nb = 2 * sizeof(double) * p->n_z;
@@ -451,6 +471,78 @@ swkb_status run(swkb_plan* p, const double* u0, int q0, int n, double* out_dev, 
     if (!fresh) TRY(reduce_to_u<T>(p, true));
     TRY(emit(0));
   }
+  return SWKB_OK;
+}
+
+void drop_graphs(swkb_plan* p) {
+  for (auto& g : p->graphs) cudaGraphExecDestroy(g.exec);
+  p->graphs.clear();
+}
+
+// Propagate as one CUDA graph: captured on first use for this (screen range,
+// buffers, timing) and replayed afterwards, so a whole propagation costs one
+// launch on the host.  Host-side copies stay outside the graph.
+template <typename T>
+swkb_status run_graph(swkb_plan* p, const double* u0, int q0, int n, double* dst, int snap) {
+  swkb_plan::Graph* g = nullptr;
+  for (auto& e : p->graphs)
+    if (e.q0 == q0 && e.n == n && e.snap == snap && e.in == u0 && e.out == dst &&
+        e.timing == (int)p->timing)
+      g = &e;
+  if (!g) {
+    if (p->graphs.size() >= 8) drop_graphs(p);
+    const swkb_plan_stats before = p->stats;
+    p->marks.clear();
+    CK(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+    swkb_status st = enqueue<T>(p, u0, q0, n, dst, nullptr, snap);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(p->stream, &graph);
+    if (st == SWKB_OK && ec != cudaSuccess)
+      st = fail(SWKB_ERR_CUDA, "stream capture failed: %s", cudaGetErrorString(ec));
+    cudaGraphExec_t exec = nullptr;
+    if (st == SWKB_OK) {
+      const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+      if (ei != cudaSuccess)
+        st = fail(SWKB_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(ei));
+    }
+    if (graph) cudaGraphDestroy(graph);
+    swkb_plan::Graph e{q0, n, snap, (int)p->timing, u0, dst, exec, p->marks, {}};
+    e.delta.launches = p->stats.launches - before.launches;
+    e.delta.screens = p->stats.screens - before.screens;
+    for (int kk = 0; kk < SWKB_KERNEL_KINDS; ++kk)
+      e.delta.kernel_launches[kk] = p->stats.kernel_launches[kk] - before.kernel_launches[kk];
+    p->stats = before;
+    p->marks.clear();
+    if (st != SWKB_OK) {
+      cudaGetLastError();
+      return st;
+    }
+    p->graphs.push_back(e);
+    g = &p->graphs.back();
+  }
+  CK(cudaGraphLaunch(g->exec, p->stream));
+  p->marks.insert(p->marks.end(), g->marks.begin(), g->marks.end());
+  p->stats.launches += g->delta.launches;
+  p->stats.screens += g->delta.screens;
+  for (int kk = 0; kk < SWKB_KERNEL_KINDS; ++kk)
+    p->stats.kernel_launches[kk] += g->delta.kernel_launches[kk];
+  return SWKB_OK;
+}
+
+template <typename T>
+swkb_status run(swkb_plan* p, const double* u0, int q0, int n, double* out_dev, double* out_host,
+                int snap) {
+  // graphs need a capturable stream and device-side outputs (snapshots to
+  // host memory interleave copies, which run directly instead)
+  if (p->use_graphs && p->stream != nullptr && (out_dev || snap <= 0)) {
+    double* dst = out_dev ? out_dev : p->io;
+    TRY(run_graph<T>(p, u0, q0, n, dst, snap));
+    if (!out_dev)
+      CK(cudaMemcpyAsync(out_host, p->io, 2 * sizeof(double) * p->n_z, cudaMemcpyDeviceToHost,
+                         p->stream));
+    return read_status(p);
+  }
+  TRY(enqueue<T>(p, u0, q0, n, out_dev, out_host, snap));
   return read_status(p);
 }
 
@@ -518,6 +610,7 @@ void release(swkb_plan* p) {
   int cur = 0;
   cudaGetDevice(&cur);
   cudaSetDevice(p->device);
+  drop_graphs(p);
   for (void* ptr : p->allocs) cudaFree(ptr);
   for (cudaEvent_t e : p->events) cudaEventDestroy(e);
   if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
@@ -568,6 +661,59 @@ const char* swkb_status_string(swkb_status s) {
 }  // extern "C"
 
 namespace {
+
+// Launch shapes chosen per plan: resummation tile (PW points per lane, tile
+// of 32 PW grid points), resummation CTAs per SM (mode groups), DFT split
+// N = N1 N2.
+struct Tiling {
+  int PW, ctas_per_sm, N1;
+};
+
+bool valid_tiling(const swkb_plan* p, const Tiling& t) {
+  if (t.PW != 2 && t.PW != 4 && t.PW != 8 && t.PW != 16) return false;
+  if (32 * t.PW > (p->sym ? p->N / 2 : p->N)) return false;
+  if (t.N1 < 1 || t.N1 > 64 || (t.N1 & (t.N1 - 1)) || t.N1 > p->N / 32) return false;
+  return t.ctas_per_sm >= 1;
+}
+
+Tiling default_tiling(const swkb_plan* p) {
+  Tiling t;
+  t.PW = p->R >= 8 ? 8 : (p->R >= 2 ? 4 : 2);
+  while (32 * t.PW > (p->sym ? p->N / 2 : p->N)) t.PW /= 2;
+  t.ctas_per_sm = 6;
+  // N1 ~ sqrt(M): pass 1 costs N N1, pass 2 M N2
+  t.N1 = 1;
+  while (t.N1 * t.N1 * 2 < p->M && t.N1 < p->N / 32 && t.N1 < 64) t.N1 *= 2;
+  return t;
+}
+
+std::vector<Tiling> tiling_candidates(const swkb_plan* p) {
+  const Tiling d = default_tiling(p);
+  std::vector<Tiling> out;
+  for (int pw : {d.PW / 2, d.PW, d.PW * 2})
+    for (int c : {4, 6, 8, 12})
+      for (int n1 : {d.N1, d.N1 * 2}) {
+        const Tiling t{pw, c, n1};
+        if (valid_tiling(p, t)) out.push_back(t);
+      }
+  return out;
+}
+
+void apply_tiling(swkb_plan* p, const Tiling& t) {
+  p->PW = t.PW;
+  p->TM = 32 * t.PW;
+  p->n_tiles = p->N / p->TM;
+  p->n_tiles_run = p->sym ? p->n_tiles / 2 + 1 : p->n_tiles;
+  p->wcap = 4 * p->TM / p->R + 8;   // rays per tile window: up to 4x compression
+  p->ctas_per_sm = t.ctas_per_sm;
+  const int target_ctas = p->sms * t.ctas_per_sm;
+  p->n_groups = std::max(1, std::min(p->M, (target_ctas + p->n_tiles_run - 1) / p->n_tiles_run));
+  p->modes_per_group = (p->M + p->n_groups - 1) / p->n_groups;
+  p->n_groups = (p->M + p->modes_per_group - 1) / p->modes_per_group;
+  p->N1 = t.N1;
+  p->N2 = p->N / p->N1;
+  p->log2N2 = ilog2(p->N2);
+}
 
 // Validate the arguments and derive every size of the plan (host only).
 swkb_status configure(swkb_plan* p, const swkb_profile* prof, double k, const swkb_domain* dom,
@@ -622,11 +768,6 @@ swkb_status configure(swkb_plan* p, const swkb_profile* prof, double k, const sw
   p->absorber_frac = opt.absorber_frac;
   if (!(p->absorber_frac >= 0 && p->absorber_frac < 1))
     return fail(SWKB_ERR_INVALID_ARG, "absorber_frac must be in [0, 1)");
-  // DFT split N = N1 N2 with N1 ~ sqrt(M): pass 1 costs N N1, pass 2 M N2
-  p->N1 = 1;
-  while (p->N1 * p->N1 * 2 < p->M && p->N1 < p->N / 32 && p->N1 < 64) p->N1 *= 2;
-  p->N2 = p->N / p->N1;
-  p->log2N2 = ilog2(p->N2);
   // medium
   p->n_cols = prof->n_cols; p->n_p = prof->n_p; p->n_int = prof->n_p - 1;
   p->z0p = prof->z0_p; p->dzp = prof->dz_p;
@@ -671,21 +812,22 @@ swkb_status configure(swkb_plan* p, const swkb_profile* prof, double k, const sw
   // is even / odd, so only n >= 0 is marched and only z >= z_a summed
   p->sym = p->mirror != 0;
   p->Mr = p->sym ? p->n_max + 1 : p->M;
-  // resummation tiling
-  p->PW = p->R >= 8 ? 8 : (p->R >= 2 ? 4 : 2);
-  while (32 * p->PW > (p->sym ? p->N / 2 : p->N)) p->PW /= 2;
-  p->TM = 32 * p->PW;
-  p->n_tiles = p->N / p->TM;
-  p->n_tiles_run = p->sym ? p->n_tiles / 2 + 1 : p->n_tiles;
-  p->wcap = 4 * p->TM / p->R + 8;   // rays per tile window: up to 4x compression
   p->device = opt.device;
   CK(cudaSetDevice(p->device));
-  int sms = 0;
-  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
-  const int target_ctas = sms * 6;
-  p->n_groups = std::max(1, std::min(p->M, (target_ctas + p->n_tiles_run - 1) / p->n_tiles_run));
-  p->modes_per_group = (p->M + p->n_groups - 1) / p->n_groups;
-  p->n_groups = (p->M + p->modes_per_group - 1) / p->modes_per_group;
+  CK(cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device));
+  p->autotune = opt.autotune != 0;
+  const Tiling def = default_tiling(p);
+  apply_tiling(p, def);
+  p->alloc_groups = p->n_groups;
+  p->alloc_tiles = p->n_tiles;
+  if (p->autotune) {
+    for (const Tiling& t : tiling_candidates(p)) {
+      apply_tiling(p, t);
+      p->alloc_groups = std::max(p->alloc_groups, p->n_groups);
+      p->alloc_tiles = std::max(p->alloc_tiles, p->n_tiles);
+    }
+    apply_tiling(p, def);
+  }
   return SWKB_OK;
 }
 
@@ -698,9 +840,9 @@ size_t device_bytes(const swkb_plan* p) {
   b += 3 * (size_t)p->M * T + (size_t)p->M * V;                     // mode tables
   b += (size_t)p->N * V;                                            // twiddles
   if (p->absorber_frac > 0) b += (size_t)p->N * T;                  // absorber
-  b += (size_t)p->N * V * (2 + (size_t)p->n_groups) + (size_t)p->M * V;  // u, Y, partials, c
+  b += (size_t)p->N * V * (2 + (size_t)p->alloc_groups) + (size_t)p->M * V;  // u, Y, partials, c
   b += 3 * (size_t)p->NRT * p->Mr * T;                              // rays
-  b += (size_t)(p->n_tiles + 1) * p->Mr * sizeof(int) * (p->sym ? 2 : 1);
+  b += (size_t)(p->alloc_tiles + 1) * p->Mr * sizeof(int) * (p->sym ? 2 : 1);
   b += 16 + 2 * (size_t)std::max(p->N, p->n_z) * sizeof(double);   // status, io
   return b;
 }
@@ -726,6 +868,75 @@ swkb_status finish_t(swkb_plan* p, bool fresh) {
   const int off = p->mirror ? p->n_z : 0;
   TRY(timed(p, SWKB_KERNEL_OUTPUT, 1,
             [&] { return launch_output<T>((const V*)p->u, off, p->n_z, p->io, p->stream); }));
+  return SWKB_OK;
+}
+
+std::mutex g_tune_mutex;
+std::map<std::string, Tiling> g_tune_cache;
+
+std::string tune_key(const swkb_plan* p) {
+  char buf[256];
+  snprintf(buf, sizeof(buf), "%d/%d/%d/%d/%d/%d/%d/%d/%d/%d/%d", p->precision, p->device, p->sms,
+           p->N, p->M, p->Mr, p->NRT, p->R, p->Nt, p->sym, p->n_cols > 1);
+  return buf;
+}
+
+// Time every candidate tiling on this plan's own buffers (two screens each,
+// after one warm-up screen, CUDA events on the plan's stream) and keep the
+// fastest; the choice is cached per shape for the rest of the process.
+template <typename T>
+swkb_status autotune_plan(swkb_plan* p) {
+  using V = typename C2<T>::type;
+  const std::string key = tune_key(p);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      apply_tiling(p, it->second);
+      return SWKB_OK;
+    }
+  }
+  int dev = 0, optin = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  CK(cudaMemsetAsync(p->u, 0, (size_t)p->N * sizeof(V), p->stream));
+  CK(cudaMemsetAsync(p->part, 0, (size_t)p->alloc_groups * p->N * sizeof(V), p->stream));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  Tiling best = default_tiling(p);
+  float best_ms = 1e30f;
+  swkb_status st = SWKB_OK;
+  for (const Tiling& t : tiling_candidates(p)) {
+    apply_tiling(p, t);
+    if (resum_smem_bytes<T>(p->wcap, p->TM) > (size_t)optin) continue;
+    st = launch_screen<T>(p, 0, true);
+    if (st != SWKB_OK) break;
+    cudaEventRecord(e0, p->stream);
+    for (int r = 1; r <= 2 && st == SWKB_OK; ++r) st = launch_screen<T>(p, r, false);
+    if (st != SWKB_OK) break;
+    cudaEventRecord(e1, p->stream);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      st = fail(SWKB_ERR_CUDA, "autotune timing failed: %s", cudaGetErrorString(e));
+      break;
+    }
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = t;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  apply_tiling(p, best);
+  CK(cudaMemsetAsync(p->status, 0, sizeof(unsigned), p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  memset(&p->stats, 0, sizeof(p->stats));
+  if (st != SWKB_OK) return st;
+  std::lock_guard<std::mutex> lk(g_tune_mutex);
+  g_tune_cache[key] = best;
   return SWKB_OK;
 }
 
@@ -795,6 +1006,8 @@ swkb_status swkb_plan_create(const swkb_profile* prof, double k, const swkb_doma
     swkb_plan* p = new swkb_plan();
     struct Guard { swkb_plan*& p; ~Guard() { if (p) release(p); } } guard{p};
     TRY(configure(p, prof, k, dom, n_z, screen_dx, opt));
+    const char* ge = getenv("SWKB_GRAPHS");
+    p->use_graphs = !(ge && ge[0] == '0');
     if (opt.cuda_stream) {
       p->stream = (cudaStream_t)opt.cuda_stream;
     } else {
@@ -804,6 +1017,10 @@ swkb_status swkb_plan_create(const swkb_profile* prof, double k, const swkb_doma
     swkb_status st = p->precision == SWKB_FP64 ? build_device<double>(p, prof)
                                                : build_device<float>(p, prof);
     if (st != SWKB_OK) return st;
+    if (p->autotune) {
+      st = p->precision == SWKB_FP64 ? autotune_plan<double>(p) : autotune_plan<float>(p);
+      if (st != SWKB_OK) return st;
+    }
     CK(cudaStreamSynchronize(p->stream));
     *out = p;
     p = nullptr;  // disarm guard
@@ -827,6 +1044,7 @@ swkb_status swkb_plan_get_info(const swkb_plan* p, swkb_plan_info* info) {
   info->mode_groups = p->n_groups;
   info->march_modes = p->Mr;
   info->resum_points = p->n_tiles_run * p->TM;
+  info->fft_n1 = p->N1;
   info->dz = p->dz;
   info->period = p->L;
   info->eps_ref = p->eps_ref;
@@ -878,9 +1096,9 @@ swkb_status swkb_debug_screen(swkb_plan* p, int32_t q, const double* u_full, dou
 
 void swkb_plan_destroy(swkb_plan* p) { release(p); }
 
-swkb_status swkb_plan_set_timing(swkb_plan* p, int32_t on) {
+swkb_status swkb_plan_set_timing(swkb_plan* p, int32_t kinds) {
   if (!p) return fail(SWKB_ERR_INVALID_ARG, "NULL plan");
-  p->timing = on != 0;
+  p->timing = (unsigned)kinds & ((1u << SWKB_KERNEL_KINDS) - 1u);
   p->marks.clear();
   memset(&p->stats, 0, sizeof(p->stats));
   return SWKB_OK;

@@ -67,7 +67,7 @@ class swkb_plan_info(ctypes.Structure):
     _fields_ = [("n_fft", c_int32), ("n_max", c_int32), ("n_modes", c_int32),
                 ("n_rays", c_int32), ("n_ghost", c_int32), ("n_rays_total", c_int32),
                 ("tile_points", c_int32), ("mode_groups", c_int32), ("march_modes", c_int32),
-                ("resum_points", c_int32), ("dz", c_double),
+                ("resum_points", c_int32), ("fft_n1", c_int32), ("dz", c_double),
                 ("period", c_double), ("eps_ref", c_double), ("device_bytes", c_size_t)]
 
 
@@ -177,7 +177,7 @@ def swkb_options_default() -> swkb_options:
     return o
 
 
-def options_for(problem, precision=SWKB_FP64, stream=None, device=0) -> swkb_options:
+def options_for(problem, precision=SWKB_FP64, stream=None, device=0, autotune=False) -> swkb_options:
     o = swkb_options_default()
     o.precision = precision
     o.theta_max = float(problem.theta_max)
@@ -187,6 +187,7 @@ def options_for(problem, precision=SWKB_FP64, stream=None, device=0) -> swkb_opt
     o.absorber_frac = float(problem.absorber_frac)
     o.cuda_stream = stream
     o.device = device
+    o.autotune = 1 if autotune else 0
     return o
 
 
@@ -219,8 +220,23 @@ def swkb_plan_destroy(plan):
     lib().swkb_plan_destroy(plan)
 
 
-def swkb_plan_set_timing(plan, on: bool):
-    check(lib().swkb_plan_set_timing(plan, 1 if on else 0))
+TIME_ALL = (1 << len(KERNEL_KINDS)) - 1
+
+
+def swkb_plan_set_timing(plan, kinds):
+    """kinds: True (all kernel kinds), False (off), or an int bit mask /
+    an iterable of kind names ("march", "resum", ...)."""
+    if kinds is True:
+        mask = TIME_ALL
+    elif kinds is False or kinds is None:
+        mask = 0
+    elif isinstance(kinds, int):
+        mask = kinds
+    else:
+        mask = 0
+        for k in kinds:
+            mask |= 1 << KERNEL_KINDS.index(k)
+    check(lib().swkb_plan_set_timing(plan, int(mask)))
 
 
 def swkb_plan_get_stats(plan) -> dict:
@@ -327,10 +343,10 @@ class Server:
 class Plan:
     """A plan for one workloads.Problem (or equivalent fields)."""
 
-    def __init__(self, problem, precision=SWKB_FP64, stream=None, device=0):
+    def __init__(self, problem, precision=SWKB_FP64, stream=None, device=0, autotune=False):
         self.problem = problem
         dom = swkb_domain(problem.z_a, problem.z_b, problem.x0, problem.bc)
-        self.options = options_for(problem, precision, stream, device)
+        self.options = options_for(problem, precision, stream, device, autotune)
         self.handle = swkb_plan_create(problem.profile, problem.k, dom, problem.n_z,
                                        problem.dx, self.options)
         self.info = swkb_plan_get_info(self.handle)
@@ -364,8 +380,8 @@ class Plan:
             n_screens = self.problem.n_screens
         return swkb_propagate(self.handle, u0_ptr, q0, n_screens, out_ptr, snapshot_every, 1)
 
-    def set_timing(self, on: bool):
-        swkb_plan_set_timing(self.handle, on)
+    def set_timing(self, kinds=True):
+        swkb_plan_set_timing(self.handle, kinds)
 
     def stats(self) -> dict:
         return swkb_plan_get_stats(self.handle)

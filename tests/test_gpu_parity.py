@@ -267,3 +267,13 @@ def test_paper_scale_mixed_vs_fp64_first_screens():
     a = swkb.Plan(pb).propagate(n_screens=20)
     b = swkb.Plan(pb, swkb.SWKB_MIXED).propagate(n_screens=20)
     assert rel_l2(b, a) < MIXED_TOL
+
+
+@pytest.mark.parametrize("prec,tol", [(swkb.SWKB_FP64, FP64_TOL), (swkb.SWKB_MIXED, MIXED_TOL)])
+def test_autotuned_plan_parity(prec, tol):
+    """The autotuner only changes launch shapes: an autotuned plan still
+    matches the oracle."""
+    pb = duct_small()
+    plan = swkb.Plan(pb, prec, autotune=True)
+    assert plan.info.tile_points in (64, 128, 256, 512) and plan.info.fft_n1 >= 1
+    assert rel_l2(plan.propagate(), duct_small_oracle()) < tol
