@@ -199,18 +199,20 @@ typedef struct {
   uint64_t launches;                         /* kernel launches since reset    */
   uint64_t screens;                          /* screens advanced since reset   */
   uint64_t kernel_launches[SWKB_KERNEL_KINDS];
-  double kernel_ms[SWKB_KERNEL_KINDS];       /* device time per kind, from CUDA
+  uint64_t kernel_timed[SWKB_KERNEL_KINDS];  /* launches that were timed      */
+  double kernel_ms[SWKB_KERNEL_KINDS];       /* device time of the timed
+                                                launches per kind, from CUDA
                                                 events recorded on the plan's
-                                                stream around each launch (only
-                                                while timing is on)            */
+                                                stream around each of them     */
 } swkb_plan_stats;
 
 /* kinds: bit mask of kernel kinds (1 << SWKB_KERNEL_*; SWKB_TIME_ALL for
    every kind, 0 to stop) whose launches get CUDA events recorded around them
-   on the plan's stream, accumulating per-kind device time.  Resets the
-   counters.  Each timed launch adds two event records to the stream. */
+   on the plan's stream, accumulating per-kind device time; every >= 1 times
+   one launch in `every` of each selected kind (each timed launch adds two
+   event records to the stream).  Resets the counters. */
 #define SWKB_TIME_ALL ((1 << SWKB_KERNEL_KINDS) - 1)
-swkb_status swkb_plan_set_timing(swkb_plan* plan, int32_t kinds);
+swkb_status swkb_plan_set_timing(swkb_plan* plan, int32_t kinds, int32_t every);
 swkb_status swkb_plan_get_stats(const swkb_plan* plan, swkb_plan_stats* stats);
 
 /*

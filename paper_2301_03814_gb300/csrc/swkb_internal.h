@@ -103,6 +103,11 @@ struct FftArgs {
   typename C2<T>::type* Y;           // [N1][N2]
   int N, N1, N2, log2N2, n_max;
   int mirror;                        // 0, or +-1: the field is even / odd
+  // pass 1 may form the field itself from the resummation partials (absorber
+  // and reflection as in ReduceArgs) instead of reading u
+  const typename C2<T>::type* part;  // [n_part][N] or nullptr: read u
+  int n_part, sym;
+  const T* W;
   T inv_N;
   const typename C2<T>::type* ephi;  // [M] exp(i Phi_n)
   typename C2<T>::type* c;           // [M]

@@ -380,13 +380,11 @@ __global__ void __launch_bounds__(256) k_march_x2(const MarchArgs<float> p) {
 // ----------------------------------------------------------------------------
 // Landing of ray j in grid units: g_j = (j - G) R + d_j.  Tile t starts at
 // grid point t TM; jlo[t][i] = the j with g_j <= t TM < g_{j+1}.
+// One landing pair (j, j + 1) of column i: order and coverage checks, and
+// the tile starts the pair brackets.  Returns status bits.
 template <typename T>
-__global__ void k_bracket(const BracketArgs<T> p) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y;
-  if (i >= p.Mr || j >= p.NRT - 1) return;
-  const T d0 = p.d[(long long)j * p.Mr + i];
-  const T d1 = p.d[(long long)(j + 1) * p.Mr + i];
+__device__ __forceinline__ unsigned bracket_pair(const BracketArgs<T>& p, int i, int j, T d0,
+                                                 T d1) {
   const int b0 = (j - p.G) * p.R;   // |b0| <= N + G R < 2^31
   const int b1 = b0 + p.R;
   unsigned st = 0;
@@ -397,10 +395,7 @@ __global__ void k_bracket(const BracketArgs<T> p) {
     if (j == 2 && !(d0 < T(-b0))) st |= ST_COVER;                 // g_2 < 0
     if (j + 1 == p.NRT - 1 && !(d1 >= T(p.N - b1))) st |= ST_COVER;  // g_{NRT-1} >= N
   }
-  if (st) {
-    atomicOr(p.status, st);
-    return;
-  }
+  if (st) return st;
   const int TM = p.TM;
   const float inv_tm = 1.0f / (float)TM;   // exact (TM is a power of two)
   {
@@ -418,8 +413,8 @@ __global__ void k_bracket(const BracketArgs<T> p) {
     for (int t = t0; t <= t1; ++t) p.jlo[(long long)t * p.Mr + i] = j;
   }
   if (p.sym) {
-    // mirror family: ray j' = NRT - 1 - j ... lands at N - g.  Its bracket of
-    // tile start t TM is j' when g_j < N - t TM <= g_{j+1}.
+    // mirror family: its bracket of tile start t TM is ray NRT - 1 - j when
+    // g_j < N - t TM <= g_{j+1}
     int t0 = (int)ceilf(((float)p.N - (float)b1 - (float)d1) * inv_tm);
     int t1 = (int)ceilf(((float)p.N - (float)b0 - (float)d0) * inv_tm) - 1;
     t0 = min(max(t0, -1), p.n_tiles + 1);
@@ -433,6 +428,27 @@ __global__ void k_bracket(const BracketArgs<T> p) {
     t1 = min(t1, p.n_tiles);
     for (int t = t0; t <= t1; ++t) p.jlo_neg[(long long)t * p.Mr + i] = p.NRT - 1 - j;
   }
+  return 0;
+}
+
+// One thread per landing pair (measured faster than longer per-thread runs:
+// the kernel is latency-bound and wants the parallelism).
+constexpr int BRACKET_RUN = 1;
+
+template <typename T>
+__global__ void k_bracket(const BracketArgs<T> p) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j0 = blockIdx.y * BRACKET_RUN;
+  if (i >= p.Mr) return;
+  const int j1 = min(j0 + BRACKET_RUN, p.NRT - 1);   // pairs (j, j + 1), j < j1
+  unsigned st = 0;
+  T d0 = p.d[(long long)j0 * p.Mr + i];
+  for (int j = j0; j < j1; ++j) {
+    const T d1 = p.d[(long long)(j + 1) * p.Mr + i];
+    st |= bracket_pair(p, i, j, d0, d1);
+    d0 = d1;
+  }
+  if (st) atomicOr(p.status, st);
 }
 
 // ----------------------------------------------------------------------------
@@ -751,6 +767,32 @@ __device__ __forceinline__ typename C2<T>::type cmul(typename C2<T>::type a,
 // w_{N1}^{n1 k1} for all k1.  N1 <= 64.
 constexpr int FFT1_COLS = 8;
 
+// Field value at grid point m formed from the resummation partials: the sum
+// over mode groups times the absorber, with the reflection of grounded plans
+// (same arithmetic as k_reduce).
+template <typename T>
+__device__ __forceinline__ typename C2<T>::type field_from_parts(const FftArgs<T>& p, int m) {
+  using V = typename C2<T>::type;
+  const int half = p.N >> 1;
+  const int src = (p.sym && m > 0 && m < half) ? p.N - m : m;
+  V s;
+  s.x = T(0); s.y = T(0);
+  for (int g = 0; g < p.n_part; ++g) {
+    const V v = p.part[(long long)g * p.N + src];
+    s.x += v.x; s.y += v.y;
+  }
+  if (p.W) { const T w = p.W[src]; s.x *= w; s.y *= w; }
+  if (p.sym) {
+    const T sg = T(p.mirror);
+    if (m == 0 || m == half) {
+      s.x = T(0.5) * (s.x + sg * s.x); s.y = T(0.5) * (s.y + sg * s.y);
+    } else if (m < half) {
+      s.x = sg * s.x; s.y = sg * s.y;
+    }
+  }
+  return s;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_fft1(const FftArgs<T> p) {
   using V = typename C2<T>::type;
@@ -760,7 +802,8 @@ __global__ void __launch_bounds__(256) k_fft1(const FftArgs<T> p) {
   const int c0 = blockIdx.x * FFT1_COLS;
   for (int e = threadIdx.x; e < p.N1 * FFT1_COLS; e += blockDim.x) {
     const int n1 = e / FFT1_COLS, c = e % FFT1_COLS;
-    tile[e] = p.u[(long long)n1 * p.N2 + c0 + c];
+    const int m = n1 * p.N2 + c0 + c;
+    tile[e] = p.part ? field_from_parts(p, m) : p.u[m];
   }
   for (int k = threadIdx.x; k < p.N1; k += blockDim.x) w1[k] = p.tw[(long long)k * p.N2];
   __syncthreads();
@@ -880,7 +923,7 @@ cudaError_t launch_march<float>(const MarchArgs<float>& a, bool multi_column, cu
 
 template <typename T>
 cudaError_t launch_bracket(const BracketArgs<T>& a, cudaStream_t s) {
-  dim3 grid((a.Mr + 127) / 128, a.NRT - 1);
+  dim3 grid((a.Mr + 127) / 128, (a.NRT - 1 + BRACKET_RUN - 1) / BRACKET_RUN);
   k_bracket<T><<<grid, 128, 0, s>>>(a);
   return cudaGetLastError();
 }

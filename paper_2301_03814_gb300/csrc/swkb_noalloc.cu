@@ -120,6 +120,10 @@ extern "C" swkb_status swkb_modes_noalloc(const double* u, int32_t n_fft, int32_
   f.N = n_fft;
   f.N2 = n_fft < 2048 ? n_fft : 2048;   // N1 = n_fft / N2 <= 32
   f.mirror = 0;
+  f.part = nullptr;   // the caller's field is read directly
+  f.n_part = 0;
+  f.sym = 0;
+  f.W = nullptr;
   f.N1 = n_fft / f.N2;
   f.log2N2 = 0;
   while ((1 << f.log2N2) < f.N2) ++f.log2N2;

@@ -74,6 +74,7 @@ class swkb_plan_info(ctypes.Structure):
 class swkb_plan_stats(ctypes.Structure):
     _fields_ = [("launches", c_uint64), ("screens", c_uint64),
                 ("kernel_launches", c_uint64 * len(KERNEL_KINDS)),
+                ("kernel_timed", c_uint64 * len(KERNEL_KINDS)),
                 ("kernel_ms", c_double * len(KERNEL_KINDS))]
 
 
@@ -108,7 +109,7 @@ def lib():
         L.swkb_propagate.argtypes = [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_int32,
                                      c_int32]
         L.swkb_debug_screen.argtypes = [c_void_p, c_int32] + [c_void_p] * 6
-        L.swkb_plan_set_timing.argtypes = [c_void_p, c_int32]
+        L.swkb_plan_set_timing.argtypes = [c_void_p, c_int32, c_int32]
         L.swkb_plan_get_stats.argtypes = [c_void_p, POINTER(swkb_plan_stats)]
         L.swkb_plan_destroy.argtypes = [c_void_p]
         L.swkb_plan_destroy.restype = None
@@ -223,9 +224,10 @@ def swkb_plan_destroy(plan):
 TIME_ALL = (1 << len(KERNEL_KINDS)) - 1
 
 
-def swkb_plan_set_timing(plan, kinds):
+def swkb_plan_set_timing(plan, kinds, every=1):
     """kinds: True (all kernel kinds), False (off), or an int bit mask /
-    an iterable of kind names ("march", "resum", ...)."""
+    an iterable of kind names ("march", "resum", ...); every: time one launch
+    in `every` of each selected kind."""
     if kinds is True:
         mask = TIME_ALL
     elif kinds is False or kinds is None:
@@ -236,7 +238,7 @@ def swkb_plan_set_timing(plan, kinds):
         mask = 0
         for k in kinds:
             mask |= 1 << KERNEL_KINDS.index(k)
-    check(lib().swkb_plan_set_timing(plan, int(mask)))
+    check(lib().swkb_plan_set_timing(plan, int(mask), int(every)))
 
 
 def swkb_plan_get_stats(plan) -> dict:
@@ -244,6 +246,7 @@ def swkb_plan_get_stats(plan) -> dict:
     check(lib().swkb_plan_get_stats(plan, byref(st)))
     return {"launches": int(st.launches), "screens": int(st.screens),
             "kernel_launches": {k: int(st.kernel_launches[i]) for i, k in enumerate(KERNEL_KINDS)},
+            "kernel_timed": {k: int(st.kernel_timed[i]) for i, k in enumerate(KERNEL_KINDS)},
             "kernel_ms": {k: float(st.kernel_ms[i]) for i, k in enumerate(KERNEL_KINDS)}}
 
 
@@ -380,8 +383,8 @@ class Plan:
             n_screens = self.problem.n_screens
         return swkb_propagate(self.handle, u0_ptr, q0, n_screens, out_ptr, snapshot_every, 1)
 
-    def set_timing(self, kinds=True):
-        swkb_plan_set_timing(self.handle, kinds)
+    def set_timing(self, kinds=True, every=1):
+        swkb_plan_set_timing(self.handle, kinds, every)
 
     def stats(self) -> dict:
         return swkb_plan_get_stats(self.handle)

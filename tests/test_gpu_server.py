@@ -147,3 +147,20 @@ def test_invalid_and_oversized_requests():
     assert st == swkb.SWKB_OK
     assert srv.poll(t, timeout_ms=60_000)[0] == swkb.SWKB_ERR_OOM
     srv.close()
+
+
+def test_uneven_batch_mixed_matches_fp64():
+    """Instances drawn like the 64-instance uneven batch (first 5 screens),
+    run together through the server in both precisions: the mixed result of
+    every instance is within 1e-4 rel-L2 of its FP64 result."""
+    from oracle.swkb_oracle import rel_l2
+    batch = [pb.with_(n_screens=min(pb.n_screens, 5)) for pb in w.batch_uneven(seed=4, n=8)]
+    srv = swkb.Server(64 * GB, max_slots=8)
+    t_mixed = [srv.submit(pb, swkb.SWKB_MIXED)[1] for pb in batch]
+    t_fp64 = [srv.submit(pb, swkb.SWKB_FP64)[1] for pb in batch]
+    for pb, a, b in zip(batch, t_mixed, t_fp64):
+        sa, ua = srv.poll(a, timeout_ms=300_000)
+        sb, ub = srv.poll(b, timeout_ms=300_000)
+        assert sa == swkb.SWKB_OK and sb == swkb.SWKB_OK, swkb.swkb_last_error()
+        assert rel_l2(ua, ub) < 1e-4, pb.name
+    srv.close()
