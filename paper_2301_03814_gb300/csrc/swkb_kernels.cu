@@ -534,8 +534,10 @@ __device__ __forceinline__ void cubic_through(T f0, T f1, T f2, T f3, T r21, T r
   b3 = d0123;
 }
 
+// FP32: 7 CTAs per SM (the register budget that keeps the one-mode-ahead
+// prefetch without losing occupancy); FP64 keeps its registers
 template <typename T, int PW>
-__global__ void __launch_bounds__(RESUM_WARPS * 32) k_resum(const ResumArgs<T> p) {
+__global__ void __launch_bounds__(RESUM_WARPS * 32, sizeof(T) == 4 ? 7 : 1) k_resum(const ResumArgs<T> p) {
   using V = typename C2<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
@@ -563,44 +565,99 @@ __global__ void __launch_bounds__(RESUM_WARPS * 32) k_resum(const ResumArgs<T> p
 #pragma unroll
   for (int q = 0; q < PW; ++q) { accr[q] = T(0); acci[q] = T(0); }
 
-  for (int i = i0 + warp; i < i1; i += RESUM_WARPS) {
-    // grounded: mode n < 0 is the mirror image of mode -n (column -n); its
-    // ray j' is ray NRT - j' of mode -n, landing at N - g
+  // Software pipeline over this warp's modes: the bracket entries are
+  // loaded two modes ahead and the ray window (landing offset, phase,
+  // amplitude; the first 32 rays) one mode ahead into registers, so their
+  // global-memory latency overlaps the current mode's arithmetic.
+  // grounded: mode n < 0 is the mirror image of mode -n (column -n); its
+  // ray j' is ray NRT - j' of mode -n, landing at N - g
+  constexpr int PF = 1;
+  T rd[PF], rph[PF], ra[PF];
+  auto column = [&](int i, bool& mir) {
     const int n = i - p.n_max;
-    const bool mirrored = p.sym && n < 0;
-    const int col = p.sym ? (n < 0 ? -n : n) : i;
-    const int* jt = mirrored ? p.jlo_neg : p.jlo;
-    const int jl = __ldg(jt + (long long)tile * p.Mr + col);
-    const int jh = __ldg(jt + (long long)(tile + 1) * p.Mr + col);
-    // A bracket table left inconsistent by a failed screen (already flagged
-    // by k_bracket) must not send the reads out of [0, NRT).
-    if (jl < (mirrored ? 2 : 1) || jh < jl || jh > p.NRT - 3) continue;
+    mir = p.sym && n < 0;
+    return p.sym ? (n < 0 ? -n : n) : i;
+  };
+  auto load_head = [&](int i, int& jl, int& jh) {
+    jl = -1; jh = -1;
+    if (i >= i1) return;
+    bool mir;
+    const int col = column(i, mir);
+    const int* jt = mir ? p.jlo_neg : p.jlo;
+    jl = __ldg(jt + (long long)tile * p.Mr + col);
+    jh = __ldg(jt + (long long)(tile + 1) * p.Mr + col);
+  };
+  // A bracket table left inconsistent by a failed screen (already flagged by
+  // k_bracket) must not send the reads out of [0, NRT); a window wider than
+  // the tile's capacity means rays compressed beyond it (flagged here).
+  auto head_ok = [&](int i, int jl, int jh) {
+    if (i >= i1) return false;
+    bool mir;
+    column(i, mir);
+    if (jl < (mir ? 2 : 1) || jh < jl || jh > p.NRT - 3) return false;
+    if (jh - jl + 4 > wcap) { st |= ST_CAUSTIC; return false; }
+    return true;
+  };
+  // ray index of window slot w (mirrored families run backwards)
+  auto ray_of = [&](bool mir, int jb, int w) { return mir ? p.NRT - jb - w : jb + w; };
+  auto prefetch = [&](int i, int jl, int jh) {
+    bool mir;
+    const int col = column(i, mir);
+    const int jb = jl - 1, W = jh - jl + 4;
+#pragma unroll
+    for (int r = 0; r < PF; ++r) {
+      const int w = lane + 32 * r;
+      if (w < W) {
+        const long long o = (long long)ray_of(mir, jb, w) * p.Mr + col;
+        rd[r] = __ldg(p.d + o);
+        rph[r] = __ldg(p.ph + o);
+        ra[r] = __ldg(p.a + o);
+      }
+    }
+  };
+
+  int i = i0 + warp;
+  int jl_c, jh_c, jl_n, jh_n;
+  load_head(i, jl_c, jh_c);
+  load_head(i + RESUM_WARPS, jl_n, jh_n);
+  bool ok_c = head_ok(i, jl_c, jh_c);
+  if (ok_c) prefetch(i, jl_c, jh_c);
+  for (; i < i1; i += RESUM_WARPS) {
+    const bool ok = ok_c;
+    const int jl = jl_c, jh = jh_c;
+    bool mirrored;
+    const int col = column(i, mirrored);
     const int jb = jl - 1;
     const int W = jh - jl + 4;
-    if (W > wcap) {            // rays compressed beyond the tile's capacity
-      st |= ST_CAUSTIC;
-      continue;
-    }
+    const int base = mirrored ? p.N - m0 - (p.NRT - jb - p.G) * p.R : (jb - p.G) * p.R - m0;
+    const T dsign = mirrored ? T(-1) : T(1);
     const V cn = p.c[i];
-    const unsigned nn = (unsigned)n;
+    const unsigned nn = (unsigned)(i - p.n_max);
     __syncwarp();
-    if (!mirrored) {
-      const int base = (jb - p.G) * p.R - m0;
-      for (int w = lane; w < W; w += 32) {
-        const long long o = (long long)(jb + w) * p.Mr + col;
-        s_X[w] = T(base + w * p.R) + __ldg(p.d + o);
-        s_ph[w] = __ldg(p.ph + o);
-        s_a[w] = __ldg(p.a + o);
+    if (ok) {
+#pragma unroll
+      for (int r = 0; r < PF; ++r) {
+        const int w = lane + 32 * r;
+        if (w < W) {
+          s_X[w] = T(base + w * p.R) + dsign * rd[r];
+          s_ph[w] = rph[r];
+          s_a[w] = ra[r];
+        }
       }
-    } else {
-      const int base = p.N - m0 - (p.NRT - jb - p.G) * p.R;
-      for (int w = lane; w < W; w += 32) {
-        const long long o = (long long)(p.NRT - jb - w) * p.Mr + col;
-        s_X[w] = T(base + w * p.R) - __ldg(p.d + o);
+      for (int w = lane + 32 * PF; w < W; w += 32) {   // beyond the prefetched rounds
+        const long long o = (long long)ray_of(mirrored, jb, w) * p.Mr + col;
+        s_X[w] = T(base + w * p.R) + dsign * __ldg(p.d + o);
         s_ph[w] = __ldg(p.ph + o);
         s_a[w] = __ldg(p.a + o);
       }
     }
+    // issue the next mode's window and the following mode's brackets
+    jl_c = jl_n;
+    jh_c = jh_n;
+    ok_c = head_ok(i + RESUM_WARPS, jl_c, jh_c);
+    if (ok_c) prefetch(i + RESUM_WARPS, jl_c, jh_c);
+    load_head(i + 2 * RESUM_WARPS, jl_n, jh_n);
+    if (!ok) continue;
     __syncwarp();
     for (int w = 1 + lane; w <= W - 3; w += 32) {
       const T X0 = s_X[w - 1], X1 = s_X[w], X2 = s_X[w + 1], X3 = s_X[w + 2];
