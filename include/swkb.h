@@ -111,6 +111,12 @@ typedef struct {
                              fastest; cached per shape for the process       */
   void* cuda_stream;      /* cudaStream_t to run on; NULL = a library stream  */
   int32_t device;         /* CUDA device ordinal                              */
+  int32_t reuse_rays;     /* 1: for a range-independent medium (one table
+                             column) march the rays once per propagate call
+                             and reuse them on every screen: the ray data
+                             depend only on the medium slab, not on the
+                             field, so results are identical (0 = march every
+                             screen, the default)                             */
 } swkb_options;
 
 typedef struct {

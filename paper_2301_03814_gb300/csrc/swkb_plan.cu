@@ -84,6 +84,8 @@ struct swkb_plan {
   std::vector<double> x_cols;
   int stage_rows = 1;  // screens q >= stage_rows - 1 share the last row
   bool autotune = false;
+  bool reuse_rays = false;   // one table column and opted in: march once per call
+  bool rays_ready = false;   // (within the current enqueue sequence)
   std::vector<double> pbar;  // host copy of P_bar_n (FP64)
   std::vector<double> ephi;  // exp(i k dx P_bar_n), interleaved
   // device
@@ -405,10 +407,15 @@ swkb_status launch_screen(swkb_plan* p, int q, bool u_fresh) {
   TRY(timed(p, SWKB_KERNEL_FFT, p->N1 > 1 ? 2 : 1, [&] { return launch_fft<T>(f, s); }));
   const MarchArgs<T> ma = march_args<T>(p, q);
   const bool multi = p->n_cols > 1;
-  TRY(timed(p, SWKB_KERNEL_MARCH, 1, [&] { return launch_march<T>(ma, multi, s); }));
+  // a range-independent medium gives every screen the same rays: with
+  // reuse_rays they are marched (and bracketed) once per enqueue sequence
+  const bool march = !(p->reuse_rays && p->rays_ready);
+  if (march)
+    TRY(timed(p, SWKB_KERNEL_MARCH, 1, [&] { return launch_march<T>(ma, multi, s); }));
   BracketArgs<T> b{(const T*)p->rd, p->Mr, p->NRT, p->G, p->R, p->N, p->TM, p->n_tiles,
                    p->jlo, p->sym, p->jlo_neg, p->status};
-  TRY(timed(p, SWKB_KERNEL_BRACKET, 1, [&] { return launch_bracket<T>(b, s); }));
+  if (march) TRY(timed(p, SWKB_KERNEL_BRACKET, 1, [&] { return launch_bracket<T>(b, s); }));
+  p->rays_ready = true;
   ResumArgs<T> ra;
   ra.d = (const T*)p->rd; ra.ph = (const T*)p->rph; ra.a = (const T*)p->ra; ra.jlo = p->jlo;
   ra.jlo_neg = p->jlo_neg;
@@ -453,6 +460,7 @@ template <typename T>
 swkb_status enqueue(swkb_plan* p, const double* u0, int q0, int n, double* out_dev,
                     double* out_host, int snap) {
   using V = typename C2<T>::type;
+  p->rays_ready = false;
   const int off = p->mirror ? p->n_z : 0;
   const size_t nb = 2 * sizeof(double) * p->n_z;
   TRY(timed(p, SWKB_KERNEL_INIT, 1,
@@ -568,6 +576,7 @@ swkb_status debug_screen(swkb_plan* p, int q, const double* u_full, double* c, d
   CK(cudaMemcpyAsync(p->io, u_full, 2 * sizeof(double) * N, cudaMemcpyHostToDevice, p->stream));
   TRY(timed(p, SWKB_KERNEL_INIT, 1,
             [&] { return launch_init<T>(p->io, N, N, 0, (V*)p->u, p->stream); }));
+  p->rays_ready = false;
   TRY(launch_screen<T>(p, q, true));
   TRY(reduce_to_u<T>(p, false));
   std::vector<V> hc(M), hu(N);
@@ -830,6 +839,7 @@ swkb_status configure(swkb_plan* p, const swkb_profile* prof, double k, const sw
   CK(cudaSetDevice(p->device));
   CK(cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device));
   p->autotune = opt.autotune != 0;
+  p->reuse_rays = opt.reuse_rays != 0 && p->n_cols == 1;
   const Tiling def = default_tiling(p);
   apply_tiling(p, def);
   p->alloc_groups = p->n_groups;
@@ -868,6 +878,7 @@ namespace {
 template <typename T>
 swkb_status begin_t(swkb_plan* p, const double* u0_host) {
   using V = typename C2<T>::type;
+  p->rays_ready = false;
   CK(cudaMemcpyAsync(p->io, u0_host, 2 * sizeof(double) * p->n_z, cudaMemcpyHostToDevice,
                      p->stream));
   TRY(timed(p, SWKB_KERNEL_INIT, 1,
@@ -923,6 +934,7 @@ swkb_status autotune_plan(swkb_plan* p) {
   swkb_status st = SWKB_OK;
   for (const Tiling& t : tiling_candidates(p)) {
     apply_tiling(p, t);
+    p->rays_ready = false;   // brackets depend on the tile size
     if (resum_smem_bytes<T>(p->wcap, p->TM) > (size_t)optin) continue;
     st = launch_screen<T>(p, 0, true);
     if (st != SWKB_OK) break;

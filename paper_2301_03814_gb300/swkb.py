@@ -60,7 +60,8 @@ class swkb_domain(ctypes.Structure):
 class swkb_options(ctypes.Structure):
     _fields_ = [("precision", c_int32), ("theta_max", c_double), ("n_max", c_int32),
                 ("ray_stride", c_int32), ("rk4_steps", c_int32), ("absorber_frac", c_double),
-                ("autotune", c_int32), ("cuda_stream", c_void_p), ("device", c_int32)]
+                ("autotune", c_int32), ("cuda_stream", c_void_p), ("device", c_int32),
+                ("reuse_rays", c_int32)]
 
 
 class swkb_plan_info(ctypes.Structure):
@@ -178,7 +179,8 @@ def swkb_options_default() -> swkb_options:
     return o
 
 
-def options_for(problem, precision=SWKB_FP64, stream=None, device=0, autotune=False) -> swkb_options:
+def options_for(problem, precision=SWKB_FP64, stream=None, device=0, autotune=False,
+                reuse_rays=False) -> swkb_options:
     o = swkb_options_default()
     o.precision = precision
     o.theta_max = float(problem.theta_max)
@@ -189,6 +191,7 @@ def options_for(problem, precision=SWKB_FP64, stream=None, device=0, autotune=Fa
     o.cuda_stream = stream
     o.device = device
     o.autotune = 1 if autotune else 0
+    o.reuse_rays = 1 if reuse_rays else 0
     return o
 
 
@@ -346,10 +349,11 @@ class Server:
 class Plan:
     """A plan for one workloads.Problem (or equivalent fields)."""
 
-    def __init__(self, problem, precision=SWKB_FP64, stream=None, device=0, autotune=False):
+    def __init__(self, problem, precision=SWKB_FP64, stream=None, device=0, autotune=False,
+                 reuse_rays=False):
         self.problem = problem
         dom = swkb_domain(problem.z_a, problem.z_b, problem.x0, problem.bc)
-        self.options = options_for(problem, precision, stream, device, autotune)
+        self.options = options_for(problem, precision, stream, device, autotune, reuse_rays)
         self.handle = swkb_plan_create(problem.profile, problem.k, dom, problem.n_z,
                                        problem.dx, self.options)
         self.info = swkb_plan_get_info(self.handle)

@@ -277,3 +277,21 @@ def test_autotuned_plan_parity(prec, tol):
     plan = swkb.Plan(pb, prec, autotune=True)
     assert plan.info.tile_points in (64, 128, 256, 512) and plan.info.fft_n1 >= 1
     assert rel_l2(plan.propagate(), duct_small_oracle()) < tol
+
+
+@pytest.mark.parametrize("prec", [swkb.SWKB_FP64, swkb.SWKB_MIXED])
+def test_reuse_rays_identical_for_range_independent_media(prec):
+    """The ray data depend only on the medium slab: with one table column,
+    marching once per propagation gives bit-identical fields; with several
+    columns the option is ignored."""
+    pb = duct_small()
+    a = swkb.Plan(pb, prec).propagate()
+    plan = swkb.Plan(pb, prec, reuse_rays=True)
+    plan.set_timing(True)
+    b = plan.propagate()
+    st = plan.stats()
+    assert np.array_equal(a, b)
+    assert st["kernel_launches"]["march"] == 1 and st["kernel_launches"]["resum"] == pb.n_screens
+    c1 = w.config_unit_periodic(n_screens=6)
+    assert np.array_equal(swkb.Plan(c1, prec, reuse_rays=True).propagate(),
+                          swkb.Plan(c1, prec).propagate())
