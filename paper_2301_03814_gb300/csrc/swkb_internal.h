@@ -23,8 +23,14 @@ template <> struct C2<double> { using type = double2; };
 
 // Quintic medium table: per column, per z interval i, the monomial
 // coefficients a0..a5 of eps(z0 + (i + t) h) - eps_ref in t in [0, 1]
-// (8 slots per interval, the last two unused).  Reflection about z_mirror for
-// grounded domains.
+// (8 slots per interval, the last two unused).
+//   FP64 plans: the profile's n_int intervals from z0 = z_a; grounded domains
+//   reflect z about z_mirror before the lookup.
+//   FP32 plans: the reflection is stored instead (grounded domains: the
+//   mirror images of the n_int intervals below z_a, then the n_int intervals
+//   above), followed by one interval continuing the last one, so that a
+//   position exactly at the top has a t = 0 entry; n_int counts the intervals
+//   before that pad and top = n_int as a float.
 template <typename T>
 struct Medium {
   const T* coef;
@@ -33,6 +39,7 @@ struct Medium {
   T z0, inv_h, inv_h2;
   int mirrored;
   T z_mirror;
+  T top;
 };
 
 // Per-screen RK4 stage columns: stage l = 0 .. 2 N_t sits at x_q + l h / 2;
@@ -54,6 +61,7 @@ struct MarchArgs {
   int mode_off;     // marched mode r is mode index r + mode_off (n = r + mode_off - n_max)
   int NRT, G, R, Nt;
   T z_lo, dz, inv_dz, h, k_over_2pi;
+  T u_lo, u_dz;     // FP32 table position of grid point 0 and per grid point
   T* out_d;         // [NRT][Mr] landing offset from the launch grid point, grid units
   T* out_ph;        // [NRT][Mr] residual phase k (r - x P_bar) / (2 pi), turns
   T* out_a;         // [NRT][Mr] amplitude factor sqrt(P0 / (P1 Z_s))

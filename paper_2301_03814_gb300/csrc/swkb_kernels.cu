@@ -261,16 +261,66 @@ struct Ray2 {
   f2 dz, dQ, rh, Zs, Qs;
 };
 
+// FP32 medium lookup at table position u (intervals from the table origin;
+// the table stores the reflection, so there is no mirror step).  Returns
+// p(t), p'(t) and p''(t)/2 of the interval's quintic (derivatives in t).
+// u outside [0, top] or NaN flags ST_RANGE and is evaluated at the clamped
+// position.  floor(u) comes from one round-down add of 1.5 * 2^23 (exact for
+// 0 <= u < 2^22), keeping the conversion units free.
+__device__ __forceinline__ void horner5(const float* q, float t, float& e, float& d1, float& d2) {
+  float a0, a1, a2, a3, a4, a5;
+  load6<float>(q, a0, a1, a2, a3, a4, a5);
+  float b = a5 * t + a4;
+  float c2 = a5;
+  float c1 = a5 * t + b;
+  b = b * t + a3;
+  c2 = c2 * t + c1; c1 = c1 * t + b; b = b * t + a2;
+  c2 = c2 * t + c1; c1 = c1 * t + b; b = b * t + a1;
+  c2 = c2 * t + c1; c1 = c1 * t + b; b = b * t + a0;
+  e = b; d1 = c1; d2 = c2;
+}
+
 template <bool MULTI>
-__device__ __forceinline__ Ray2 rhs2(const MarchArgs<float>& p, int l, f2 s, f2 kap, f2 m2kap,
-                                     f2 mkap, f2 pb, f2 mpb, float pb2, f2 pb2v, const Ray2& y,
-                                     unsigned& st) {
-  float za, zb;
-  sp2(add2(s, y.dz), za, zb);
-  float ea, eza, ezza, eb, ezb, ezzb;
-  medium_eval<float, MULTI>(p, l, za, ea, eza, ezza, st);
-  medium_eval<float, MULTI>(p, l, zb, eb, ezb, ezzb, st);
-  const f2 e = mk2(ea, eb), ez = mk2(eza, ezb), ezz = mk2(ezza, ezzb);
+__device__ __forceinline__ void med32(const MarchArgs<float>& p, int l, float u, float& e,
+                                      float& d1, float& d2, unsigned& st) {
+  const float uc = fminf(fmaxf(u, 0.f), p.med.top);
+  if (uc != u) st |= ST_RANGE;
+  const float v = __fadd_rd(uc, 12582912.f);
+  const int i = (int)(__float_as_uint(v) - 0x4B400000u);
+  const float t = uc - (v - 12582912.f);
+  if (!MULTI) {
+    horner5(p.med.coef + (long long)i * 8, t, e, d1, d2);
+  } else {
+    const int c = __ldg(p.st.c + l);
+    const float th = __ldg(p.st.th + l);
+    const float* q = p.med.coef + (long long)c * p.med.col_stride + (long long)i * 8;
+    if (th == 0.f) {
+      horner5(q, t, e, d1, d2);
+    } else if (th == 1.f) {
+      horner5(q + p.med.col_stride, t, e, d1, d2);
+    } else {
+      float e0, e1, f0, f1, g0, g1;
+      horner5(q, t, e0, f0, g0);
+      horner5(q + p.med.col_stride, t, e1, f1, g1);
+      e = (1.f - th) * e0 + th * e1;
+      d1 = (1.f - th) * f0 + th * f1;
+      d2 = (1.f - th) * g0 + th * g1;
+    }
+  }
+}
+
+// x-form right-hand side for two rays; u2 = their table positions.
+template <bool MULTI>
+__device__ __forceinline__ Ray2 rhs2(const MarchArgs<float>& p, int l, f2 u2, f2 kap, f2 m2kap,
+                                     f2 mkap, f2 pb, f2 mpb, float pb2, f2 pb2v, f2 ih, f2 ih2,
+                                     const Ray2& y, unsigned& st) {
+  float ua, ub;
+  sp2(u2, ua, ub);
+  float ea, d1a, d2a, eb, d1b, d2b;
+  med32<MULTI>(p, l, ua, ea, d1a, d2a, st);
+  med32<MULTI>(p, l, ub, eb, d1b, d2b, st);
+  const f2 e = mk2(ea, eb);
+  const f2 ez = mul2(mk2(d1a, d1b), ih), ezz = mul2(mk2(d2a, d2b), ih2);
   const f2 Q = add2(kap, y.dQ);
   const f2 D = fma2(y.dQ, sub2(m2kap, y.dQ), e);           // e - dQ (2 kappa + dQ)
   float P2a, P2b;
@@ -309,23 +359,30 @@ __device__ __forceinline__ f2 rk4_sum(f2 y, f2 h6, f2 k1, f2 k2, f2 k3, f2 k4) {
   return fma2(h6, add2(fma2(two, k3, fma2(two, k2, k1)), k4), y);
 }
 
+// Thread t marches rays q and q + NH of mode r, t = q Mr + r (NH = ceil(NRT / 2)):
+// a warp's lanes are consecutive modes at one launch height (their table
+// reads stay within a few intervals) and no lane idles at the end of a row.
 template <bool MULTI>
 __global__ void __launch_bounds__(256) k_march_x2(const MarchArgs<float> p) {
-  const int r = blockIdx.x * 32 + threadIdx.x;
-  const int ja = blockIdx.y * 16 + threadIdx.y;
-  const int jb = ja + 8;
-  if (r >= p.Mr || ja >= p.NRT) return;
+  const int NH = (p.NRT + 1) >> 1;
+  const int t = blockIdx.x * 256 + threadIdx.x;
+  if (t >= p.Mr * NH) return;
+  const int ja = t / p.Mr;
+  const int r = t - ja * p.Mr;
+  const int jb = ja + NH;
   const bool has_b = jb < p.NRT;
   unsigned st = 0;
   const int i = r + p.mode_off;
   const float kap = p.kappa[i], pb = p.pbar[i], pb2 = p.pbar2[i];
-  const float sa = p.z_lo + float((ja - p.G) * p.R) * p.dz;
-  const float sb = has_b ? p.z_lo + float((jb - p.G) * p.R) * p.dz : sa;
-  const f2 s = mk2(sa, sb), kv = bc2(kap), m2kap = bc2(-2.f * kap), mkap = bc2(-kap);
+  // launch heights in table intervals
+  const float ua = fmaf(float((ja - p.G) * p.R), p.u_dz, p.u_lo);
+  const float ub = has_b ? fmaf(float((jb - p.G) * p.R), p.u_dz, p.u_lo) : ua;
+  const f2 s = mk2(ua, ub), kv = bc2(kap), m2kap = bc2(-2.f * kap), mkap = bc2(-kap);
   const f2 pbv = bc2(pb), mpb = bc2(-pb), pb2v = bc2(pb2);
+  const f2 ih = bc2(p.med.inv_h), ih2 = bc2(p.med.inv_h2);
   float e0a, e0b, t0, t1;
-  medium_eval<float, MULTI>(p, 0, sa, e0a, t0, t1, st);
-  medium_eval<float, MULTI>(p, 0, sb, e0b, t0, t1, st);
+  med32<MULTI>(p, 0, ua, e0a, t0, t1, st);
+  med32<MULTI>(p, 0, ub, e0b, t0, t1, st);
   float P0a = pb2 + e0a, P0b = pb2 + e0b;
   if (!(P0a > 0.f)) { st |= ST_TURNING; P0a = pb2; }
   if (!(P0b > 0.f)) { st |= ST_TURNING; P0b = pb2; }
@@ -334,29 +391,36 @@ __global__ void __launch_bounds__(256) k_march_x2(const MarchArgs<float> p) {
   const f2 zero = bc2(0.f);
   Ray2 y{zero, zero, zero, bc2(1.f), zero};
   const f2 h = bc2(p.h), hh = bc2(0.5f * p.h), h6 = bc2(p.h / 6.f);
+  // table position of a ray: launch position + dz / h_table
+  const auto pos = [&](const Ray2& w) { return fma2(w.dz, ih, s); };
   for (int n = 0; n < p.Nt; ++n) {
-    const Ray2 k1 = rhs2<MULTI>(p, 2 * n, s, kv, m2kap, mkap, pbv, mpb, pb2, pb2v, y, st);
-    const Ray2 k2 = rhs2<MULTI>(p, 2 * n + 1, s, kv, m2kap, mkap, pbv, mpb, pb2, pb2v,
-                                axpy2(y, hh, k1), st);
-    const Ray2 k3 = rhs2<MULTI>(p, 2 * n + 1, s, kv, m2kap, mkap, pbv, mpb, pb2, pb2v,
-                                axpy2(y, hh, k2), st);
-    const Ray2 k4 = rhs2<MULTI>(p, 2 * n + 2, s, kv, m2kap, mkap, pbv, mpb, pb2, pb2v,
-                                axpy2(y, h, k3), st);
+    const Ray2 k1 = rhs2<MULTI>(p, 2 * n, pos(y), kv, m2kap, mkap, pbv, mpb, pb2, pb2v, ih,
+                                ih2, y, st);
+    const Ray2 y2 = axpy2(y, hh, k1);
+    const Ray2 k2 = rhs2<MULTI>(p, 2 * n + 1, pos(y2), kv, m2kap, mkap, pbv, mpb, pb2, pb2v,
+                                ih, ih2, y2, st);
+    const Ray2 y3 = axpy2(y, hh, k2);
+    const Ray2 k3 = rhs2<MULTI>(p, 2 * n + 1, pos(y3), kv, m2kap, mkap, pbv, mpb, pb2, pb2v,
+                                ih, ih2, y3, st);
+    const Ray2 y4 = axpy2(y, h, k3);
+    const Ray2 k4 = rhs2<MULTI>(p, 2 * n + 2, pos(y4), kv, m2kap, mkap, pbv, mpb, pb2, pb2v,
+                                ih, ih2, y4, st);
     y.dz = rk4_sum(y.dz, h6, k1.dz, k2.dz, k3.dz, k4.dz);
     y.dQ = rk4_sum(y.dQ, h6, k1.dQ, k2.dQ, k3.dQ, k4.dQ);
     y.rh = rk4_sum(y.rh, h6, k1.rh, k2.rh, k3.rh, k4.rh);
     y.Zs = rk4_sum(y.Zs, h6, k1.Zs, k2.Zs, k3.Zs, k4.Zs);
     y.Qs = rk4_sum(y.Qs, h6, k1.Qs, k2.Qs, k3.Qs, k4.Qs);
   }
-  float dza, dzb, dQa, dQb, rha, rhb, Zsa, Zsb;
+  float dza, dzb, dQa, dQb, rha, rhb, Zsa, Zsb, u1a, u1b;
   sp2(y.dz, dza, dzb);
   sp2(y.dQ, dQa, dQb);
   sp2(y.rh, rha, rhb);
   sp2(y.Zs, Zsa, Zsb);
+  sp2(pos(y), u1a, u1b);
   if (!(Zsa > 0.f) || !(Zsb > 0.f)) st |= ST_CAUSTIC;
   float e1a, e1b;
-  medium_eval<float, MULTI>(p, 2 * p.Nt, sa + dza, e1a, t0, t1, st);
-  medium_eval<float, MULTI>(p, 2 * p.Nt, sb + dzb, e1b, t0, t1, st);
+  med32<MULTI>(p, 2 * p.Nt, u1a, e1a, t0, t1, st);
+  med32<MULTI>(p, 2 * p.Nt, u1b, e1b, t0, t1, st);
   float P1a = pb2 + e1a - dQa * (2.f * kap + dQa);
   float P1b = pb2 + e1b - dQb * (2.f * kap + dQb);
   if (!(P1a > 0.f)) { st |= ST_TURNING; P1a = pb2; }
@@ -971,8 +1035,8 @@ cudaError_t launch_march(const MarchArgs<T>& a, bool multi_column, cudaStream_t 
 
 template <>
 cudaError_t launch_march<float>(const MarchArgs<float>& a, bool multi_column, cudaStream_t s) {
-  dim3 block(32, 8);
-  dim3 grid((a.Mr + 31) / 32, (a.NRT + 15) / 16);
+  const long long threads = (long long)a.Mr * ((a.NRT + 1) / 2);
+  const dim3 block(256), grid((unsigned)((threads + 255) / 256));
   if (multi_column) k_march_x2<true><<<grid, block, 0, s>>>(a);
   else k_march_x2<false><<<grid, block, 0, s>>>(a);
   return cudaGetLastError();

@@ -189,6 +189,9 @@ swkb_status status_from_bits(unsigned bits) {
   return SWKB_OK;
 }
 
+// Intervals of the FP32 medium table of one column (layout in swkb_internal.h).
+int table32_intervals(const swkb_plan* p) { return (p->mirror ? 2 : 1) * p->n_int + 1; }
+
 template <typename T>
 swkb_status build_device(swkb_plan* p, const swkb_profile* prof) {
   using V = typename C2<T>::type;
@@ -214,7 +217,37 @@ swkb_status build_device(swkb_plan* p, const swkb_profile* prof) {
         o[5] = 6.0 * A - 3.0 * B + 0.5 * C;
       }
     }
-    TRY(upload<T>(p, &p->coef, coef));
+    if (sizeof(T) == 8) {
+      TRY(upload<T>(p, &p->coef, coef));
+    } else {
+      // FP32 layout: reflected intervals below z_a (grounded), the profile's
+      // intervals, one continuation interval.  A reflected interval holds
+      // p(1 - t) and the continuation p_last(1 + t), re-expanded in t.
+      const int lo = p->mirror ? p->n_int : 0, nt = table32_intervals(p);
+      std::vector<double> c32((size_t)p->n_cols * nt * 8, 0.0);
+      static const double binom[6][6] = {{1, 0, 0, 0, 0, 0}, {1, 1, 0, 0, 0, 0},
+                                         {1, 2, 1, 0, 0, 0}, {1, 3, 3, 1, 0, 0},
+                                         {1, 4, 6, 4, 1, 0}, {1, 5, 10, 10, 5, 1}};
+      for (int c = 0; c < p->n_cols; ++c)
+        for (int k = 0; k < nt; ++k) {
+          const int i = k < lo ? lo - 1 - k : std::min(k - lo, p->n_int - 1);
+          const double sgn = k < lo ? -1.0 : 1.0;        // t -> 1 - t or t -> 1 + t
+          const bool shift = k < lo || k - lo >= p->n_int;
+          const double* a = coef.data() + ((size_t)c * p->n_int + i) * 8;
+          double* o = c32.data() + ((size_t)c * nt + k) * 8;
+          if (!shift) {
+            for (int j = 0; j < 6; ++j) o[j] = a[j];
+          } else {
+            // sum_m a_m (1 + sgn t)^m = sum_j t^j sgn^j sum_{m >= j} C(m, j) a_m
+            for (int j = 0; j < 6; ++j) {
+              double acc = 0;
+              for (int m = 5; m >= j; --m) acc += binom[m][j] * a[m];
+              o[j] = (j & 1) ? sgn * acc : acc;
+            }
+          }
+        }
+      TRY(upload<T>(p, &p->coef, c32));
+    }
   }
   // RK4 stage columns for screens 0 .. stage_rows - 1
   {
@@ -366,6 +399,20 @@ MarchArgs<T> march_args(const swkb_plan* p, int q) {
   a.med.inv_h2 = (T)(2.0 / (p->dzp * p->dzp));
   a.med.mirrored = p->mirror != 0;
   a.med.z_mirror = (T)p->z_a;
+  a.med.top = (T)p->n_int;
+  if (sizeof(T) == 4) {
+    // reflection stored in the table; positions in table intervals
+    const double z0 = p->mirror ? p->z0p - p->n_int * p->dzp : p->z0p;
+    a.med.n_int = (p->mirror ? 2 : 1) * p->n_int;
+    a.med.col_stride = (long long)table32_intervals(p) * 8;
+    a.med.z0 = (T)z0;
+    a.med.mirrored = 0;
+    a.med.top = (T)a.med.n_int;
+    a.u_lo = (T)((p->z_lo - z0) / p->dzp);
+    a.u_dz = (T)(p->dz / p->dzp);
+  } else {
+    a.u_lo = a.u_dz = T(0);
+  }
   const int S = 2 * p->Nt + 1;
   const int row = std::min(std::max(q, 0), p->stage_rows - 1);
   a.st.c = p->stage_c + (size_t)row * S;
@@ -805,6 +852,9 @@ swkb_status configure(swkb_plan* p, const swkb_profile* prof, double k, const sw
       if (fabs(prof->eps_z[(size_t)c * p->n_p]) > 1e-12 * (1.0 + mx))
         return fail(SWKB_ERR_INVALID_ARG, "grounded domains need eps_z = 0 at z_a");
   }
+  // the FP32 march finds table intervals with a round-down add (exact below 2^22)
+  if (p->precision != SWKB_FP64 && (long long)(p->mirror ? 2 : 1) * p->n_int >= (1LL << 22))
+    return fail(SWKB_ERR_INVALID_ARG, "permittivity table has too many intervals for FP32 plans");
   {
     const double reach = 1.5 * screen_dx * tan_t + 2.0 * p->dzp;
     const double s_first = p->z_lo - (double)p->G * p->R * p->dz;
@@ -859,7 +909,7 @@ swkb_status configure(swkb_plan* p, const swkb_profile* prof, double k, const sw
 size_t device_bytes(const swkb_plan* p) {
   const size_t T = p->precision == SWKB_FP64 ? 8 : 4, V = 2 * T;
   const size_t S = 2 * (size_t)p->Nt + 1;
-  size_t b = (size_t)p->n_cols * p->n_int * 8 * T;                  // medium
+  size_t b = (size_t)p->n_cols * (T == 8 ? p->n_int : table32_intervals(p)) * 8 * T;  // medium
   b += (size_t)p->stage_rows * S * (sizeof(int) + T);               // stage columns
   b += 3 * (size_t)p->M * T + (size_t)p->M * V;                     // mode tables
   b += (size_t)p->N * V;                                            // twiddles
