@@ -29,6 +29,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "swkb_internal.h"
 
 namespace swkb {
@@ -47,6 +49,25 @@ __device__ __forceinline__ void sincos_turns(float t, float* s, float* c) {
 __device__ __forceinline__ void sincos_turns(double t, double* s, double* c) {
   sincospi(2.0 * t, s, c);
 }
+
+// Exact integer/float steps of the resummation kept off the conversion units
+// in FP32: floor of |y| < 2^22 by a round-down add of 1.5 * 2^23, the float
+// of an integer k < 2^23 from its bits, and t - rint(t) for |t| < 2^22 by
+// adding and subtracting 1.5 * 2^23 (round to nearest even, as rint).  The
+// FP64 versions are the plain operations.
+__device__ __forceinline__ int ifloor_small(float y) {
+  return (int)(__float_as_uint(__fadd_rd(y, 12582912.f)) - 0x4B400000u);
+}
+__device__ __forceinline__ int ifloor_small(double y) { return (int)floor(y); }
+__device__ __forceinline__ float exact_u2f(unsigned k, float) {
+  return __uint_as_float(0x4B000000u | k) - 8388608.f;
+}
+__device__ __forceinline__ double exact_u2f(unsigned k, double) { return (double)k; }
+__device__ __forceinline__ float minus_rint(float t) {
+  const float r = (t + 12582912.f) - 12582912.f;
+  return t - r;
+}
+__device__ __forceinline__ double minus_rint(double t) { return t - rint(t); }
 
 // 1/sqrt: FP32 via the special-function unit (2 ulp), FP64 correctly-rounded
 // to 1 ulp.  Small-quotient division: FP32 fast (2 ulp), FP64 IEEE.
@@ -309,18 +330,22 @@ __device__ __forceinline__ void med32(const MarchArgs<float>& p, int l, float u,
   }
 }
 
-// x-form right-hand side for two rays; u2 = their table positions.
+// x-form right-hand side for two rays; u2 = their table positions.  With
+// he = eps_z / 2 and hee = eps_zz / 2 (table derivatives times 1 / (2 h) and
+// 1 / h^2):  z' = Q/P,  Q' = he/P,  r' - P_bar as in the scalar kernel,
+//   -P_s/P = (Q Q_s - he Z_s)/P^2,  Z_s' = (Q_s + Q (-P_s/P))/P,
+//   Q_s' = (hee Z_s + he (-P_s/P))/P.
 template <bool MULTI>
 __device__ __forceinline__ Ray2 rhs2(const MarchArgs<float>& p, int l, f2 u2, f2 kap, f2 m2kap,
-                                     f2 mkap, f2 pb, f2 mpb, float pb2, f2 pb2v, f2 ih, f2 ih2,
-                                     const Ray2& y, unsigned& st) {
+                                     f2 mkap, f2 pb, f2 mpb, float pb2, f2 pb2v, f2 ihh,
+                                     f2 mihh, f2 ihq, const Ray2& y, unsigned& st) {
   float ua, ub;
   sp2(u2, ua, ub);
   float ea, d1a, d2a, eb, d1b, d2b;
   med32<MULTI>(p, l, ua, ea, d1a, d2a, st);
   med32<MULTI>(p, l, ub, eb, d1b, d2b, st);
-  const f2 e = mk2(ea, eb);
-  const f2 ez = mul2(mk2(d1a, d1b), ih), ezz = mul2(mk2(d2a, d2b), ih2);
+  const f2 e = mk2(ea, eb), d1 = mk2(d1a, d1b);
+  const f2 he = mul2(d1, ihh), mhe = mul2(d1, mihh), hee = mul2(mk2(d2a, d2b), ihq);
   const f2 Q = add2(kap, y.dQ);
   const f2 D = fma2(y.dQ, sub2(m2kap, y.dQ), e);           // e - dQ (2 kappa + dQ)
   float P2a, P2b;
@@ -333,30 +358,23 @@ __device__ __forceinline__ Ray2 rhs2(const MarchArgs<float>& p, int l, f2 u2, f2
   const float iPa = rsqrtf(P2a), iPb = rsqrtf(P2b);
   const f2 iP = mk2(iPa, iPb);
   const f2 P = mul2(mk2(P2a, P2b), iP);
-  const f2 hiP = mul2(bc2(0.5f), iP);
   float da, db;
   sp2(add2(pb, P), da, db);
   const f2 rden = mk2(__fdividef(1.f, da), __fdividef(1.f, db));
   Ray2 d;
   d.dz = mul2(Q, iP);
-  d.dQ = mul2(ez, hiP);
+  d.dQ = mul2(he, iP);
   // (e - kappa dQ - P_bar D / (P_bar + P)) / P
   d.rh = mul2(fma2(mpb, mul2(D, rden), fma2(mkap, y.dQ, e)), iP);
-  // P_s / P = (eps_z Z_s - 2 Q Q_s) / (2 P^2)
-  const f2 PsiP = mul2(sub2(mul2(ez, y.Zs), mul2(add2(Q, Q), y.Qs)), mul2(hiP, iP));
-  d.Zs = mul2(sub2(y.Qs, mul2(Q, PsiP)), iP);
-  d.Qs = mul2(sub2(mul2(ezz, y.Zs), mul2(ez, PsiP)), hiP);
+  const f2 mPsiP = mul2(fma2(mhe, y.Zs, mul2(Q, y.Qs)), mul2(iP, iP));
+  d.Zs = mul2(fma2(Q, mPsiP, y.Qs), iP);
+  d.Qs = mul2(fma2(he, mPsiP, mul2(hee, y.Zs)), iP);
   return d;
 }
 
 __device__ __forceinline__ Ray2 axpy2(const Ray2& y, f2 a, const Ray2& k) {
   return Ray2{fma2(a, k.dz, y.dz), fma2(a, k.dQ, y.dQ), fma2(a, k.rh, y.rh), fma2(a, k.Zs, y.Zs),
               fma2(a, k.Qs, y.Qs)};
-}
-
-__device__ __forceinline__ f2 rk4_sum(f2 y, f2 h6, f2 k1, f2 k2, f2 k3, f2 k4) {
-  const f2 two = bc2(2.f);
-  return fma2(h6, add2(fma2(two, k3, fma2(two, k2, k1)), k4), y);
 }
 
 // Thread t marches rays q and q + NH of mode r, t = q Mr + r (NH = ceil(NRT / 2)):
@@ -379,7 +397,9 @@ __global__ void __launch_bounds__(256) k_march_x2(const MarchArgs<float> p) {
   const float ub = has_b ? fmaf(float((jb - p.G) * p.R), p.u_dz, p.u_lo) : ua;
   const f2 s = mk2(ua, ub), kv = bc2(kap), m2kap = bc2(-2.f * kap), mkap = bc2(-kap);
   const f2 pbv = bc2(pb), mpb = bc2(-pb), pb2v = bc2(pb2);
-  const f2 ih = bc2(p.med.inv_h), ih2 = bc2(p.med.inv_h2);
+  const float ihs = p.med.inv_h;
+  const f2 ih = bc2(ihs), ihh = bc2(0.5f * ihs), mihh = bc2(-0.5f * ihs);
+  const f2 ihq = bc2(0.5f * p.med.inv_h2);   // inv_h2 = 2 / h^2
   float e0a, e0b, t0, t1;
   med32<MULTI>(p, 0, ua, e0a, t0, t1, st);
   med32<MULTI>(p, 0, ub, e0b, t0, t1, st);
@@ -393,23 +413,25 @@ __global__ void __launch_bounds__(256) k_march_x2(const MarchArgs<float> p) {
   const f2 h = bc2(p.h), hh = bc2(0.5f * p.h), h6 = bc2(p.h / 6.f);
   // table position of a ray: launch position + dz / h_table
   const auto pos = [&](const Ray2& w) { return fma2(w.dz, ih, s); };
+  // RK4: y + h/6 k1 + h/3 k2 + h/3 k3 + h/6 k4, accumulated as the stages
+  // complete (k1..k3 need not stay live)
+  const f2 h3 = bc2(p.h / 3.f);
   for (int n = 0; n < p.Nt; ++n) {
-    const Ray2 k1 = rhs2<MULTI>(p, 2 * n, pos(y), kv, m2kap, mkap, pbv, mpb, pb2, pb2v, ih,
-                                ih2, y, st);
+    const Ray2 k1 = rhs2<MULTI>(p, 2 * n, pos(y), kv, m2kap, mkap, pbv, mpb, pb2, pb2v, ihh,
+                                mihh, ihq, y, st);
+    Ray2 acc = axpy2(y, h6, k1);
     const Ray2 y2 = axpy2(y, hh, k1);
     const Ray2 k2 = rhs2<MULTI>(p, 2 * n + 1, pos(y2), kv, m2kap, mkap, pbv, mpb, pb2, pb2v,
-                                ih, ih2, y2, st);
+                                ihh, mihh, ihq, y2, st);
+    acc = axpy2(acc, h3, k2);
     const Ray2 y3 = axpy2(y, hh, k2);
     const Ray2 k3 = rhs2<MULTI>(p, 2 * n + 1, pos(y3), kv, m2kap, mkap, pbv, mpb, pb2, pb2v,
-                                ih, ih2, y3, st);
+                                ihh, mihh, ihq, y3, st);
+    acc = axpy2(acc, h3, k3);
     const Ray2 y4 = axpy2(y, h, k3);
     const Ray2 k4 = rhs2<MULTI>(p, 2 * n + 2, pos(y4), kv, m2kap, mkap, pbv, mpb, pb2, pb2v,
-                                ih, ih2, y4, st);
-    y.dz = rk4_sum(y.dz, h6, k1.dz, k2.dz, k3.dz, k4.dz);
-    y.dQ = rk4_sum(y.dQ, h6, k1.dQ, k2.dQ, k3.dQ, k4.dQ);
-    y.rh = rk4_sum(y.rh, h6, k1.rh, k2.rh, k3.rh, k4.rh);
-    y.Zs = rk4_sum(y.Zs, h6, k1.Zs, k2.Zs, k3.Zs, k4.Zs);
-    y.Qs = rk4_sum(y.Qs, h6, k1.Qs, k2.Qs, k3.Qs, k4.Qs);
+                                ihh, mihh, ihq, y4, st);
+    y = axpy2(acc, h6, k4);
   }
   float dza, dzb, dQa, dQb, rha, rhb, Zsa, Zsb, u1a, u1b;
   sp2(y.dz, dza, dzb);
@@ -740,11 +762,12 @@ __global__ void __launch_bounds__(RESUM_WARPS * 32, sizeof(T) == 4 ? 7 : 1) k_re
     // mean landing spacing, then corrected by comparisons
     const T xf = s_X[1];
     const T inv_sp = T(W - 3) / (s_X[W - 2] - xf);
+    const T xo = -xf * inv_sp;
 #pragma unroll
     for (int q = 0; q < PW; ++q) {
       const int x = lane + 32 * q;
       const T xv = T(x);
-      int w = 1 + (int)((xv - xf) * inv_sp);
+      int w = 1 + ifloor_small(xv * inv_sp + xo);
       w = min(max(w, 1), W - 3);
       while (w > 1 && s_X[w] > xv) --w;
       while (w < W - 3 && s_X[w + 1] <= xv) ++w;
@@ -754,8 +777,7 @@ __global__ void __launch_bounds__(RESUM_WARPS * 32, sizeof(T) == 4 ? 7 : 1) k_re
       const T phv = ((b3 * tau + b2) * tau + b1) * tau + b0;
       const T av = ((a3 * tau + a2) * tau + a1) * tau + a0;
       const unsigned nm = (nn * (unsigned)(m0 + x)) & mask;
-      T t = T(nm) * invN + phv;
-      t -= rint(t);
+      const T t = minus_rint(exact_u2f(nm, T()) * invN + phv);
       T sn, cs;
       sincos_turns(t, &sn, &cs);
       const T ar = av * cn.x, ai = av * cn.y;
@@ -997,56 +1019,58 @@ __global__ void __launch_bounds__(FFT2_THREADS) k_fft2(const FftArgs<T> p) {
 // ----------------------------------------------------------------------------
 // launchers
 // ----------------------------------------------------------------------------
+namespace {
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                     Args&&... args) {
+  k<<<grid, block, smem, s>>>(std::forward<Args>(args)...);
+  return cudaGetLastError();
+}
+}  // namespace
+
 template <typename T>
 cudaError_t launch_init(const double* u0, int n_z, int N, int mirror, typename C2<T>::type* u,
                         cudaStream_t s) {
-  k_init<T><<<(N + 255) / 256, 256, 0, s>>>(u0, n_z, N, mirror, u);
-  return cudaGetLastError();
+  return launch_k(k_init<T>, dim3((N + 255) / 256), dim3(256), 0, s, u0, n_z, N, mirror, u);
 }
 
 template <typename T>
 cudaError_t launch_reduce(const ReduceArgs<T>& a, cudaStream_t s) {
   const int n = (a.mirror || a.sym) ? a.N / 2 + 1 : a.N;
-  k_reduce<T><<<(n + 255) / 256, 256, 0, s>>>(a);
-  return cudaGetLastError();
+  return launch_k(k_reduce<T>, dim3((n + 255) / 256), dim3(256), 0, s, a);
 }
 
 template <typename T>
 cudaError_t launch_fft(const FftArgs<T>& a, cudaStream_t s) {
   if (a.N1 > 1) {
     const size_t smem = (size_t)(a.N1 * FFT1_COLS + a.N1) * sizeof(typename C2<T>::type);
-    k_fft1<T><<<a.N2 / FFT1_COLS, 256, smem, s>>>(a);
-    cudaError_t e = cudaGetLastError();
+    const cudaError_t e = launch_k(k_fft1<T>, dim3(a.N2 / FFT1_COLS), dim3(256), smem, s, a);
     if (e != cudaSuccess) return e;
   }
   const int modes = a.mirror ? a.n_max + 1 : 2 * a.n_max + 1;
-  k_fft2<T><<<modes, FFT2_THREADS, 0, s>>>(a);
-  return cudaGetLastError();
+  return launch_k(k_fft2<T>, dim3(modes), dim3(FFT2_THREADS), 0, s, a);
 }
 
 template <typename T>
 cudaError_t launch_march(const MarchArgs<T>& a, bool multi_column, cudaStream_t s) {
   dim3 block(32, 8);
   dim3 grid((a.Mr + 31) / 32, (a.NRT + 7) / 8);
-  if (multi_column) k_march<T, true><<<grid, block, 0, s>>>(a);
-  else k_march<T, false><<<grid, block, 0, s>>>(a);
-  return cudaGetLastError();
+  return multi_column ? launch_k(k_march<T, true>, grid, block, 0, s, a)
+                      : launch_k(k_march<T, false>, grid, block, 0, s, a);
 }
 
 template <>
 cudaError_t launch_march<float>(const MarchArgs<float>& a, bool multi_column, cudaStream_t s) {
   const long long threads = (long long)a.Mr * ((a.NRT + 1) / 2);
   const dim3 block(256), grid((unsigned)((threads + 255) / 256));
-  if (multi_column) k_march_x2<true><<<grid, block, 0, s>>>(a);
-  else k_march_x2<false><<<grid, block, 0, s>>>(a);
-  return cudaGetLastError();
+  return multi_column ? launch_k(k_march_x2<true>, grid, block, 0, s, a)
+                      : launch_k(k_march_x2<false>, grid, block, 0, s, a);
 }
 
 template <typename T>
 cudaError_t launch_bracket(const BracketArgs<T>& a, cudaStream_t s) {
   dim3 grid((a.Mr + 127) / 128, (a.NRT - 1 + BRACKET_RUN - 1) / BRACKET_RUN);
-  k_bracket<T><<<grid, 128, 0, s>>>(a);
-  return cudaGetLastError();
+  return launch_k(k_bracket<T>, grid, dim3(128), 0, s, a);
 }
 
 template <typename T>
@@ -1063,13 +1087,12 @@ cudaError_t launch_resum(const ResumArgs<T>& a, cudaStream_t s) {
   const size_t smem = resum_smem_bytes<T>(a.wcap, a.TM);
   const int threads = RESUM_WARPS * 32;
   switch (a.PW) {
-    case 2: k_resum<T, 2><<<grid, threads, smem, s>>>(a); break;
-    case 4: k_resum<T, 4><<<grid, threads, smem, s>>>(a); break;
-    case 8: k_resum<T, 8><<<grid, threads, smem, s>>>(a); break;
-    case 16: k_resum<T, 16><<<grid, threads, smem, s>>>(a); break;
+    case 2: return launch_k(k_resum<T, 2>, dim3(grid), dim3(threads), smem, s, a);
+    case 4: return launch_k(k_resum<T, 4>, dim3(grid), dim3(threads), smem, s, a);
+    case 8: return launch_k(k_resum<T, 8>, dim3(grid), dim3(threads), smem, s, a);
+    case 16: return launch_k(k_resum<T, 16>, dim3(grid), dim3(threads), smem, s, a);
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 template <typename T>
@@ -1100,8 +1123,7 @@ cudaError_t prepare_fft_kernels() {
 template <typename T>
 cudaError_t launch_output(const typename C2<T>::type* u, int offset, int n, double* out,
                           cudaStream_t s) {
-  k_output<T><<<(n + 255) / 256, 256, 0, s>>>(u, offset, n, out);
-  return cudaGetLastError();
+  return launch_k(k_output<T>, dim3((n + 255) / 256), dim3(256), 0, s, u, offset, n, out);
 }
 
 #define SWKB_INSTANTIATE(T)                                                                     \
