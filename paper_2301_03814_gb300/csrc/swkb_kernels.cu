@@ -484,6 +484,14 @@ __device__ __forceinline__ unsigned bracket_pair(const BracketArgs<T>& p, int i,
   if (st) return st;
   const int TM = p.TM;
   const float inv_tm = 1.0f / (float)TM;   // exact (TM is a power of two)
+  // Both families bracket a tile start only if a multiple of TM lies in
+  // [g_j, g_{j+1}] (the mirror family's starts N - t TM are multiples of TM
+  // too).  Float estimate with a margin of TM / 1000, far above its rounding;
+  // the exact tests below decide the pairs that pass.
+  {
+    const float g0 = (float)b0 + (float)d0, g1 = (float)b1 + (float)d1;
+    if (floorf(g1 * inv_tm + 1e-3f) < ceilf(g0 * inv_tm - 1e-3f)) return 0;
+  }
   {
     // tile starts t TM in [g_j, g_{j+1})
     int t0 = (int)ceilf(((float)b0 + (float)d0) * inv_tm);
@@ -552,9 +560,9 @@ __global__ void k_bracket(const BracketArgs<T> p) {
 //      the tile start), phase, amplitude;
 //  (2) one lane per interval [X_w, X_{w+1}): builds the 4-point Lagrange
 //      polynomial through X_{w-1} .. X_{w+2} (Newton form, then monomial in
-//      tau = x - X_w) for phase and amplitude, and marks the tile points the
-//      interval contains in a point -> interval table;
-//  (3) every lane evaluates its points: interval lookup, two cubics, the
+//      tau = x - X_w) for phase and amplitude into a shared-memory row;
+//  (3) every lane evaluates its points: interval lookup (guessed from the
+//      mean landing spacing, corrected by comparisons), two cubics, the
 //      phase with its integer part exact (k kappa_n (z_m - z_lo) =
 //      2 pi (n m mod N) / N), sincos, complex multiply-accumulate.
 constexpr int RESUM_WARPS = 4;
@@ -892,9 +900,10 @@ __global__ void k_output(const typename C2<T>::type* __restrict__ u, int offset,
 // ----------------------------------------------------------------------------
 // (a) pruned DFT: N = N1 N2, n = n1 N2 + n2, k = k1 + N1 k2
 //   X[k1 + N1 k2] = sum_n2 w_{N2}^{n2 k2} w_N^{n2 k1} sum_n1 x[n1 N2 + n2] w_{N1}^{n1 k1}
-// pass 1 (N1 > 1): one thread per column n2, direct length-N1 DFT + twiddle;
-// pass 2: one CTA per row k1, radix-2 Stockham FFT of length N2 in shared
-// memory, writes only the kept bins |n| <= n_max as c_n.
+// pass 1 (N1 > 1): direct length-N1 DFTs down the columns n2, then the twiddle
+// w_N^{n2 k1};
+// pass 2: one CTA per kept bin n (|n| <= n_max; n >= 0 for grounded fields),
+// a direct length-N2 sum along its row k1, written as c_n.
 // ----------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ typename C2<T>::type cmul(typename C2<T>::type a,
@@ -905,7 +914,7 @@ __device__ __forceinline__ typename C2<T>::type cmul(typename C2<T>::type a,
   return r;
 }
 
-// pass 1: a CTA takes 32 consecutive columns n2 (all N1 rows, one coalesced
+// pass 1: a CTA takes FFT1_COLS consecutive columns n2 (all N1 rows, one
 // tile in shared memory) and forms Y[k1][n2] = w_N^{n2 k1} sum_n1 x[n1 N2 + n2]
 // w_{N1}^{n1 k1} for all k1.  N1 <= 64.
 constexpr int FFT1_COLS = 8;
@@ -920,8 +929,18 @@ __device__ __forceinline__ typename C2<T>::type field_from_parts(const FftArgs<T
   const int src = (p.sym && m > 0 && m < half) ? p.N - m : m;
   V s;
   s.x = T(0); s.y = T(0);
-  for (int g = 0; g < p.n_part; ++g) {
-    const V v = p.part[(long long)g * p.N + src];
+  // loads issued in batches of 8, added in group order
+  const V* q = p.part + src;
+  int g = 0;
+  for (; g + 8 <= p.n_part; g += 8) {
+    V v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = q[(long long)(g + k) * p.N];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) { s.x += v[k].x; s.y += v[k].y; }
+  }
+  for (; g < p.n_part; ++g) {
+    const V v = q[(long long)g * p.N];
     s.x += v.x; s.y += v.y;
   }
   if (p.W) { const T w = p.W[src]; s.x *= w; s.y *= w; }
@@ -989,7 +1008,25 @@ __global__ void __launch_bounds__(FFT2_THREADS) k_fft2(const FftArgs<T> p) {
   const V* row = (p.N1 > 1 ? p.Y : p.u) + (long long)k1 * p.N2;
   V acc;
   acc.x = T(0); acc.y = T(0);
-  for (int n2 = threadIdx.x; n2 < p.N2; n2 += FFT2_THREADS) {
+  // row entries and twiddles loaded 8 iterations at a time, summed in order
+  constexpr int B = 8;
+  int n2 = threadIdx.x;
+  for (; n2 + (B - 1) * FFT2_THREADS < p.N2; n2 += B * FFT2_THREADS) {
+    V rv[B], tv[B];
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      const int m = n2 + k * FFT2_THREADS;
+      const unsigned e = (unsigned)(((long long)m * k2) & (p.N2 - 1));
+      rv[k] = row[m];
+      tv[k] = twiddle2(p.tw, e, p.log2N2, p.N1);
+    }
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      const V t = cmul<T>(rv[k], tv[k]);
+      acc.x += t.x; acc.y += t.y;
+    }
+  }
+  for (; n2 < p.N2; n2 += FFT2_THREADS) {
     const unsigned e = (unsigned)(((long long)n2 * k2) & (p.N2 - 1));
     const V t = cmul<T>(row[n2], twiddle2(p.tw, e, p.log2N2, p.N1));
     acc.x += t.x; acc.y += t.y;
