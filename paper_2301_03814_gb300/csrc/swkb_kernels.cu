@@ -550,7 +550,7 @@ __global__ void k_bracket(const BracketArgs<T> p) {
 // ----------------------------------------------------------------------------
 // A CTA owns one tile of TM = 32 PW consecutive grid points and one mode
 // group; its RESUM_WARPS warps take the group's modes round-robin, each
-// summing into registers (lane l holds points l, l + 32, ...), and the CTA
+// summing into registers (lane l holds points l PW .. l PW + PW - 1), and the CTA
 // adds the warps' sums in a fixed order before writing one partial per
 // (group, point).
 //
@@ -566,7 +566,7 @@ __global__ void k_bracket(const BracketArgs<T> p) {
 //      phase with its integer part exact (k kappa_n (z_m - z_lo) =
 //      2 pi (n m mod N) / N), sincos, complex multiply-accumulate.
 constexpr int RESUM_WARPS = 4;
-constexpr int RESUM_CF = 12;      // X_w, 4 phase + 4 amplitude coefficients, 3 pad
+constexpr int RESUM_CF = 12;      // X_w, 4 phase + 4 amplitude coefficients, X_{w+1}, 2 pad
 
 template <typename T>
 __device__ __forceinline__ int resum_warp_bytes(int wcap) {
@@ -575,42 +575,49 @@ __device__ __forceinline__ int resum_warp_bytes(int wcap) {
 
 // one coefficient row (X_w, phase b0..b3, amplitude a0..a3), vector stores:
 // rows are 48 B (FP32) apart, so a quarter-warp writes 32 distinct banks
-__device__ __forceinline__ void store_cf(float* p, float X1, float b0, float b1, float b2,
-                                         float b3, float a0, float a1, float a2, float a3) {
+// Row of interval w: X_w, phase cubic b0..b3, amplitude cubic a0..a3, X_{w+1}.
+__device__ __forceinline__ void store_cf(float* p, float X1, float X2, float b0, float b1,
+                                         float b2, float b3, float a0, float a1, float a2,
+                                         float a3) {
   *reinterpret_cast<float4*>(p) = make_float4(X1, b0, b1, b2);
   *reinterpret_cast<float4*>(p + 4) = make_float4(b3, a0, a1, a2);
-  *reinterpret_cast<float4*>(p + 8) = make_float4(a3, 0.f, 0.f, 0.f);
+  *reinterpret_cast<float4*>(p + 8) = make_float4(a3, X2, 0.f, 0.f);
 }
-__device__ __forceinline__ void store_cf(double* p, double X1, double b0, double b1, double b2,
-                                         double b3, double a0, double a1, double a2, double a3) {
+__device__ __forceinline__ void store_cf(double* p, double X1, double X2, double b0, double b1,
+                                         double b2, double b3, double a0, double a1, double a2,
+                                         double a3) {
   *reinterpret_cast<double2*>(p) = make_double2(X1, b0);
   *reinterpret_cast<double2*>(p + 2) = make_double2(b1, b2);
   *reinterpret_cast<double2*>(p + 4) = make_double2(b3, a0);
   *reinterpret_cast<double2*>(p + 6) = make_double2(a1, a2);
-  *reinterpret_cast<double2*>(p + 8) = make_double2(a3, 0.0);
+  *reinterpret_cast<double2*>(p + 8) = make_double2(a3, X2);
 }
 
 template <typename T>
-__device__ __forceinline__ void load_cf(const T* p, T& X1, T& b0, T& b1, T& b2, T& b3, T& a0,
-                                        T& a1, T& a2, T& a3);
+__device__ __forceinline__ void load_cf(const T* p, T& X1, T& X2, T& b0, T& b1, T& b2, T& b3,
+                                        T& a0, T& a1, T& a2, T& a3);
 template <>
-__device__ __forceinline__ void load_cf<float>(const float* p, float& X1, float& b0, float& b1,
-                                               float& b2, float& b3, float& a0, float& a1,
-                                               float& a2, float& a3) {
+__device__ __forceinline__ void load_cf<float>(const float* p, float& X1, float& X2, float& b0,
+                                               float& b1, float& b2, float& b3, float& a0,
+                                               float& a1, float& a2, float& a3) {
   const float4 u = *reinterpret_cast<const float4*>(p);
   const float4 v = *reinterpret_cast<const float4*>(p + 4);
-  const float w = p[8];
-  X1 = u.x; b0 = u.y; b1 = u.z; b2 = u.w; b3 = v.x; a0 = v.y; a1 = v.z; a2 = v.w; a3 = w;
+  const float2 w = *reinterpret_cast<const float2*>(p + 8);
+  X1 = u.x; b0 = u.y; b1 = u.z; b2 = u.w; b3 = v.x; a0 = v.y; a1 = v.z; a2 = v.w;
+  a3 = w.x; X2 = w.y;
 }
 template <>
-__device__ __forceinline__ void load_cf<double>(const double* p, double& X1, double& b0,
-                                                double& b1, double& b2, double& b3, double& a0,
-                                                double& a1, double& a2, double& a3) {
+__device__ __forceinline__ void load_cf<double>(const double* p, double& X1, double& X2,
+                                                double& b0, double& b1, double& b2, double& b3,
+                                                double& a0, double& a1, double& a2,
+                                                double& a3) {
   const double2 u = *reinterpret_cast<const double2*>(p);
   const double2 v = *reinterpret_cast<const double2*>(p + 2);
   const double2 w = *reinterpret_cast<const double2*>(p + 4);
   const double2 x = *reinterpret_cast<const double2*>(p + 6);
-  X1 = u.x; b0 = u.y; b1 = v.x; b2 = v.y; b3 = w.x; a0 = w.y; a1 = x.x; a2 = x.y; a3 = p[8];
+  const double2 y = *reinterpret_cast<const double2*>(p + 8);
+  X1 = u.x; b0 = u.y; b1 = v.x; b2 = v.y; b3 = w.x; a0 = w.y; a1 = x.x; a2 = x.y;
+  a3 = y.x; X2 = y.y;
 }
 
 // Newton divided differences through (X1, X2, X0, X3), rewritten as a cubic
@@ -763,34 +770,41 @@ __global__ void __launch_bounds__(RESUM_WARPS * 32, sizeof(T) == 4 ? 7 : 1) k_re
                     h21, h10, b0, b1, b2, b3);
       cubic_through(s_a[w - 1], s_a[w], s_a[w + 1], s_a[w + 2], r21, r10, r32, r20, r31, r30,
                     h21, h10, a0, a1, a2, a3);
-      store_cf(s_cf + RESUM_CF * w, X1, b0, b1, b2, b3, a0, a1, a2, a3);
+      store_cf(s_cf + RESUM_CF * w, X1, X2, b0, b1, b2, b3, a0, a1, a2, a3);
     }
     __syncwarp();
-    // interval of point x: X_w <= x < X_{w+1}, w in [1, W-3]; guessed from the
-    // mean landing spacing, then corrected by comparisons
+    // Lane l sums the PW consecutive points x = l PW + q.  The interval of its
+    // first point (X_w <= x < X_{w+1}, w in [1, W-3]) is guessed from the mean
+    // landing spacing and corrected by comparisons; later points only step
+    // forward, reloading the row when they pass X_{w+1}.
     const T xf = s_X[1];
     const T inv_sp = T(W - 3) / (s_X[W - 2] - xf);
-    const T xo = -xf * inv_sp;
+    const int x0 = lane * PW;
+    const T xv0 = T(x0);
+    int w = 1 + ifloor_small(xv0 * inv_sp - xf * inv_sp);
+    w = min(max(w, 1), W - 3);
+    while (w > 1 && s_X[w] > xv0) --w;
+    while (w < W - 3 && s_X[w + 1] <= xv0) ++w;
+    T X1, X2, b0, b1, b2, b3, a0, a1, a2, a3;
+    load_cf<T>(s_cf + RESUM_CF * w, X1, X2, b0, b1, b2, b3, a0, a1, a2, a3);
+    unsigned nm = (nn * (unsigned)(m0 + x0)) & mask;
 #pragma unroll
     for (int q = 0; q < PW; ++q) {
-      const int x = lane + 32 * q;
-      const T xv = T(x);
-      int w = 1 + ifloor_small(xv * inv_sp + xo);
-      w = min(max(w, 1), W - 3);
-      while (w > 1 && s_X[w] > xv) --w;
-      while (w < W - 3 && s_X[w + 1] <= xv) ++w;
-      T X1, b0, b1, b2, b3, a0, a1, a2, a3;
-      load_cf<T>(s_cf + RESUM_CF * w, X1, b0, b1, b2, b3, a0, a1, a2, a3);
+      const T xv = T(x0 + q);
+      while (w < W - 3 && X2 <= xv) {
+        ++w;
+        load_cf<T>(s_cf + RESUM_CF * w, X1, X2, b0, b1, b2, b3, a0, a1, a2, a3);
+      }
       const T tau = xv - X1;
       const T phv = ((b3 * tau + b2) * tau + b1) * tau + b0;
       const T av = ((a3 * tau + a2) * tau + a1) * tau + a0;
-      const unsigned nm = (nn * (unsigned)(m0 + x)) & mask;
       const T t = minus_rint(exact_u2f(nm, T()) * invN + phv);
       T sn, cs;
       sincos_turns(t, &sn, &cs);
       const T ar = av * cn.x, ai = av * cn.y;
       accr[q] += ar * cs - ai * sn;
       acci[q] += ar * sn + ai * cs;
+      nm = (nm + nn) & mask;
     }
   }
   if (st) atomicOr(p.status, st);
@@ -802,7 +816,7 @@ __global__ void __launch_bounds__(RESUM_WARPS * 32, sizeof(T) == 4 ? 7 : 1) k_re
     V v;
     v.x = accr[q];
     v.y = acci[q];
-    red[warp * TM + lane + 32 * q] = v;
+    red[warp * TM + lane * PW + q] = v;
   }
   __syncthreads();
   V* out = p.part + (long long)group * p.N + m0;
@@ -1106,8 +1120,8 @@ cudaError_t launch_march<float>(const MarchArgs<float>& a, bool multi_column, cu
 
 template <typename T>
 cudaError_t launch_bracket(const BracketArgs<T>& a, cudaStream_t s) {
-  dim3 grid((a.Mr + 127) / 128, (a.NRT - 1 + BRACKET_RUN - 1) / BRACKET_RUN);
-  return launch_k(k_bracket<T>, grid, dim3(128), 0, s, a);
+  dim3 grid((a.Mr + 255) / 256, (a.NRT - 1 + BRACKET_RUN - 1) / BRACKET_RUN);
+  return launch_k(k_bracket<T>, grid, dim3(256), 0, s, a);
 }
 
 template <typename T>
