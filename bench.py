@@ -54,6 +54,8 @@ def parse_args():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="default launch shapes instead of the autotuned ones (for profiling)")
     return ap.parse_args()
 
 
@@ -210,6 +212,11 @@ def whole_job_rate(points_per_step, steps, world, t_max_s):
     return points_per_step * steps * world / t_max_s
 
 
+def rel_l2(a, b):
+    """||a - b|| / ||b|| (the mixed-vs-FP64 comparison of two GPU fields)."""
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
 def march_flops_per_ray(pb):
     # algorithmic flops of one ray (FMA = 2): per RK4 stage the medium
     # (quintic value + 2 derivatives, interval lookup, reflection: 39) and the
@@ -296,6 +303,25 @@ def serving_measurement(swkb, n_requests=48, rate_hz=20.0, seed=5, precision=Non
                     "20 screens/km, trilinear or evaporation duct, seed 5"}
 
 
+def serving_sweep(swkb, rates=(25.0, 50.0, 100.0, 200.0, 400.0), n_requests=48):
+    """The same request stream offered at increasing Poisson rates.  A rate is
+    sustained when every request completes and results leave at >= 95 % of
+    the offered rate (n_requests / (last completion - first arrival)), i.e.
+    the queue does not grow; the highest sustained rate is reported."""
+    out = []
+    best = None
+    for r in rates:
+        m = serving_measurement(swkb, n_requests=n_requests, rate_hz=r)
+        served = m["requests"] / m["wall_s"]
+        ok = m["ok"] == m["requests"] and served >= 0.95 * r
+        out.append({"offered_rate_hz": r, "served_rate_hz": served, "p50_ms": m["p50_ms"],
+                    "p99_ms": m["p99_ms"], "sustained": bool(ok)})
+        if ok:
+            best = r
+    return {"rates": out, "max_sustained_rate_hz": best, "requests_per_rate": n_requests,
+            "rule": "all complete and served rate >= 0.95 x offered"}
+
+
 def batched_measurement(swkb, n=64, screens=10, seed=4):
     """64 uneven instances (C4 draw, N_z 2^12..2^16), the first `screens`
     screens of each, all submitted at once to the server (continuous
@@ -317,7 +343,6 @@ def batched_measurement(swkb, n=64, screens=10, seed=4):
 def run_ours(args, world, rank, local):
     import torch
     from paper_2301_03814_gb300 import swkb
-    from oracle.swkb_oracle import rel_l2
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -326,8 +351,9 @@ def run_ours(args, world, rank, local):
         dist.init_process_group("nccl")
     pb = workload()
     stream = torch.cuda.Stream(device=dev)
-    plan = swkb.Plan(pb, swkb.SWKB_MIXED, stream=stream.cuda_stream, device=local, autotune=True)
-    plan64 = swkb.Plan(pb, swkb.SWKB_FP64, stream=stream.cuda_stream, device=local, autotune=True)
+    tune = not args.no_autotune
+    plan = swkb.Plan(pb, swkb.SWKB_MIXED, stream=stream.cuda_stream, device=local, autotune=tune)
+    plan64 = swkb.Plan(pb, swkb.SWKB_FP64, stream=stream.cuda_stream, device=local, autotune=tune)
     u0 = torch.from_numpy(pb.u0).to(dev)
     out = torch.empty_like(u0)
     out64 = torch.empty_like(u0)
@@ -372,8 +398,12 @@ def run_ours(args, world, rank, local):
     clocks = Clocks(local)
     torch.cuda.synchronize()
     barrier()
+    # the timed steps are the profiler window (ncu --profile-from-start off);
+    # a no-op without a profiler attached
+    torch.cuda.profiler.start()
     ts = timed(plan, out, args.steps)
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     barrier()
     clk = clocks.stop()
     st = plan.stats()
@@ -450,7 +480,7 @@ def run_ours(args, world, rank, local):
             "config": config_dict(pb, {"parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
             "e2e": e2e, "gpu_launches": int(st["launches"]),
             "tiling": {"tile_points": info.tile_points, "mode_groups": info.mode_groups,
-                       "fft_n1": info.fft_n1, "autotuned": True},
+                       "fft_n1": info.fft_n1, "autotuned": tune},
             "fp64": {"value": value64, "unit": UNIT, "ms_per_step": statistics.mean(ts64),
                      "steps": len(ts64), "kernel_ms_per_step": {k: v / len(ts64) for k, v in st64["kernel_ms"].items()}},
             "mixed_vs_fp64_rel_l2": err,
@@ -462,6 +492,7 @@ def run_ours(args, world, rank, local):
                         "min": min(ts), "max": max(ts)}}
     if world == 1 and not args.no_serving:
         line["serving"] = serving_measurement(swkb)
+        line["serving_sweep"] = serving_sweep(swkb)
         line["batched"] = batched_measurement(swkb)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(pb)

@@ -790,7 +790,7 @@ __global__ void __launch_bounds__(RESUM_WARPS * 32, sizeof(T) == 4 ? 7 : 1) k_re
     unsigned nm = (nn * (unsigned)(m0 + x0)) & mask;
 #pragma unroll
     for (int q = 0; q < PW; ++q) {
-      const T xv = T(x0 + q);
+      const T xv = xv0 + T(q);   // exact
       while (w < W - 3 && X2 <= xv) {
         ++w;
         load_cf<T>(s_cf + RESUM_CF * w, X1, X2, b0, b1, b2, b3, a0, a1, a2, a3);
@@ -810,21 +810,25 @@ __global__ void __launch_bounds__(RESUM_WARPS * 32, sizeof(T) == 4 ? 7 : 1) k_re
   if (st) atomicOr(p.status, st);
   // fixed-order sum of the warps' partial sums
   __syncthreads();
+  // per warp TM points as 32 runs of PW, each run padded to PW + 1 entries so
+  // that the lanes' stores fall in different banks
   V* red = reinterpret_cast<V*>(smem_raw);
+  const int TMP = 32 * (PW + 1);
 #pragma unroll
   for (int q = 0; q < PW; ++q) {
     V v;
     v.x = accr[q];
     v.y = acci[q];
-    red[warp * TM + lane * PW + q] = v;
+    red[warp * TMP + lane * (PW + 1) + q] = v;
   }
   __syncthreads();
   V* out = p.part + (long long)group * p.N + m0;
   for (int x = threadIdx.x; x < TM; x += blockDim.x) {
-    V sum = red[x];
+    const int xs = (x / PW) * (PW + 1) + x % PW;
+    V sum = red[xs];
 #pragma unroll
     for (int w = 1; w < RESUM_WARPS; ++w) {
-      const V v = red[w * TM + x];
+      const V v = red[w * TMP + xs];
       sum.x += v.x; sum.y += v.y;
     }
     out[x] = sum;
@@ -1128,7 +1132,8 @@ template <typename T>
 size_t resum_smem_bytes(int wcap, int tile_points) {
   const size_t per_warp = ((RESUM_CF + 3) * (size_t)wcap * sizeof(T) + 15) & ~(size_t)15;
   const size_t stage = (size_t)RESUM_WARPS * per_warp;
-  const size_t red = (size_t)RESUM_WARPS * tile_points * sizeof(typename C2<T>::type);
+  // 32 runs of PW points, each padded to PW + 1 entries
+  const size_t red = (size_t)RESUM_WARPS * (tile_points + 32) * sizeof(typename C2<T>::type);
   return stage > red ? stage : red;
 }
 
