@@ -823,7 +823,7 @@ swkb_status configure(swkb_plan* p, const swkb_profile* prof, double k, const sw
   if (opt.n_max > 0) p->n_max = opt.n_max;
   else p->n_max = (int)floor(sin(opt.theta_max) * p->L / lam * (1.0 + 1e-12));
   p->n_max = std::min(p->n_max, p->N / 2 - 1);
-  if (p->n_max < 1) return fail(SWKB_ERR_INVALID_ARG, "no propagating mode kept (n_max < 1)");
+  if (p->n_max < 0) return fail(SWKB_ERR_INVALID_ARG, "negative theta_max or n_max");
   p->M = 2 * p->n_max + 1;
   p->R = opt.ray_stride;
   if (p->R < 1 || p->N % p->R) return fail(SWKB_ERR_INVALID_ARG, "ray stride must divide N");
