@@ -51,6 +51,13 @@ also implemented, separately, by the CUDA library):
       (C^2) and linear interpolation in x between the columns bracketing x;
       at the start of a screen the right limit in x is used, at its end the
       left limit.
+  R15 fields between screens (Sec. 2.1, the remark that extra interpolation
+      points may be added for visualisation): on the planes x_q + j dx / P,
+      j = 1..P with P dividing N_t (RK4 step boundaries), the screen's modes
+      and rays marched j N_t / P steps, interpolated and summed exactly as on
+      the screen; the absorber is a screen-level device and multiplies only
+      the screen's own field (j = P); grounded fields are projected onto
+      even / odd functions like screen fields.
 
 Everything is float64.  Functions raise OracleError subclasses on R7 events.
 """
@@ -313,11 +320,14 @@ class Oracle:
         dQs = ezz * Zs / (2.0 * P) - ez * Ps / (2.0 * P * P)
         return dz, dQ, dr, dZs, dQs
 
-    def march(self, q: int, kappa: np.ndarray, s: np.ndarray):
+    def march(self, q: int, kappa: np.ndarray, s: np.ndarray, steps: int | None = None):
         """RK4 across screen q for rays (kappa, s) (arrays of one shape).
         Returns dict with landing z, Q, residual r, Z_s, Q_s, P0, P1 and the
-        amplitude factor a = sqrt(P0 / (P1 Z_s)) (R6)."""
+        amplitude factor a = sqrt(P0 / (P1 Z_s)) (R6).  steps < rk4_steps
+        stops on the plane x_q + steps h inside the screen (R15), with P1
+        evaluated there."""
         pb = self.pb
+        n_steps = pb.rk4_steps if steps is None else int(steps)
         xs = self.stage_x(q)
         h = pb.dx / pb.rk4_steps
         kappa, s = np.broadcast_arrays(np.asarray(kappa, dtype=np.float64),
@@ -334,7 +344,7 @@ class Oracle:
             raise TurningError("mode is evanescent at launch")
         P0 = np.sqrt(P0sq)
         y = (z, Q, r, Zs, Qs)
-        for i in range(pb.rk4_steps):
+        for i in range(n_steps):
             a = xs[2 * i]
             m = xs[2 * i + 1]
             b = xs[2 * i + 2]
@@ -347,7 +357,7 @@ class Oracle:
         z, Q, r, Zs, Qs = y
         if np.any(Zs <= 0.0):
             raise CausticError("Z_s <= 0 at landing")
-        e1, _, _ = self.medium.eval(xs[-1][0], xs[-1][1], z)
+        e1, _, _ = self.medium.eval(xs[2 * n_steps][0], xs[2 * n_steps][1], z)
         P1sq = e1 - Q * Q
         if np.any(P1sq <= 0):
             raise TurningError("eps - Q^2 <= 0 at landing")
@@ -393,18 +403,58 @@ class Oracle:
         c = self.modes(u)                                            # (a)
         s = self.launch_points()
         rays = self.march(q, self.kappa[:, None], s[None, :])       # (b)
-        delta = (rays["z"] - g.z_lo) / g.dz
-        m = np.arange(g.N)
-        out = np.zeros(g.N, dtype=np.complex128)
-        for i in range(len(self.n)):                                 # (c) + (d)
-            r_m, a_m = self.interpolate(delta[i], (rays["r"][i], rays["a"][i]))
-            n = int(self.n[i])
-            base = 2.0 * math.pi * ((n * m) % g.N) / g.N             # = k kappa_n (z_m - z_lo)
-            out += c[i] * a_m * np.exp(1j * (base + pb.k * r_m))
-        out = out * self.W
+        out = self.modal_sum(c, rays) * self.W                       # (c) + (d)
         if keep_rays:
             return out, c, rays
         return out
+
+    def modal_sum(self, c: np.ndarray, rays) -> np.ndarray:
+        """Eq. ray_bundle_q_plus_1 on the grid: for every mode, phase and
+        amplitude interpolated from its rays' landings (R8), then
+        sum_n c_n A_n exp(i (k kappa_n (z_m - z_lo) + k r_n))."""
+        g = self.g
+        delta = (rays["z"] - g.z_lo) / g.dz
+        m = np.arange(g.N)
+        out = np.zeros(g.N, dtype=np.complex128)
+        for i in range(len(self.n)):
+            r_m, a_m = self.interpolate(delta[i], (rays["r"][i], rays["a"][i]))
+            n = int(self.n[i])
+            base = 2.0 * math.pi * ((n * m) % g.N) / g.N             # = k kappa_n (z_m - z_lo)
+            out += c[i] * a_m * np.exp(1j * (base + self.pb.k * r_m))
+        return out
+
+    # -- fields between screens (Section 2: extra interpolation points) --------------
+    def screen_planes(self, u: np.ndarray, q: int, planes: int):
+        """Fields of screen q on the planes x_q + j dx / planes, j = 1..planes
+        (R15): the screen's modes and rays, marched j rk4_steps / planes RK4
+        steps, interpolated and summed like the screen itself.  The last plane
+        is the screen's own field (absorber applied); the planes before it are
+        the ray field between screens (no absorber)."""
+        pb = self.pb
+        if planes < 1 or pb.rk4_steps % planes:
+            raise ValueError("planes must divide rk4_steps")
+        u = self.project(u)
+        c = self.modes(u)
+        s = self.launch_points()
+        out = []
+        for j in range(1, planes + 1):
+            rays = self.march(q, self.kappa[:, None], s[None, :],
+                              steps=j * pb.rk4_steps // planes)
+            f = self.modal_sum(c, rays)
+            out.append(f * self.W if j == planes else f)
+        return out
+
+    def propagate_planes(self, u_phys: np.ndarray, q0: int, n_screens: int, planes: int):
+        """Physical fields on every plane of screens q0 .. q0+n_screens-1,
+        rows ordered (screen, plane); each screen starts from the previous
+        screen's last plane."""
+        u = self.extend(u_phys)
+        rows = []
+        for q in range(q0, q0 + n_screens):
+            fields = self.screen_planes(u, q, planes)
+            rows.extend(self.restrict(self.project(f)) for f in fields)
+            u = fields[-1]
+        return np.array(rows)
 
     def screen_points(self, u: np.ndarray, q: int, ms) -> np.ndarray:
         """The modal sum of screen q (times the absorber, before the

@@ -152,3 +152,65 @@ def pin_airy(O):
     got = O(pb).propagate(u0)
     ref = airy_field(u0, z, k, a, 100.0, np.arange(-130.0, 105.0, 0.04))
     return rel_l2(got, ref)
+
+
+def pin_planes_homogeneous(O, bc=w.BC_PERIODIC, planes=4, eps0=1.03):
+    """Fields between screens in a homogeneous medium: plane j of screen q
+    must equal the band-limited angular spectrum over (q + j / planes) dx."""
+    pb = w.config_homogeneous(eps0=eps0, n_z=128, height=32.0, dx=15.0, n_screens=2, bc=bc,
+                              ray_stride=1, rk4_steps=8)
+    o = O(pb)
+    rows = o.propagate_planes(pb.u0, 0, pb.n_screens, planes)
+    g = o.g
+    err = 0.0
+    for q in range(pb.n_screens):
+        for j in range(1, planes + 1):
+            d = (q + j / planes) * pb.dx
+            if bc == w.BC_PERIODIC:
+                ref = angular_spectrum(pb.u0, pb.k, g.L, d, g.n_max, eps0)
+            else:
+                sgn = 1.0 if bc == w.BC_NEUMANN else -1.0
+                n = pb.n_z
+                full = np.zeros(2 * n, complex)
+                full[n:] = pb.u0
+                full[n - np.arange(1, n)] = sgn * pb.u0[1:]
+                ref = angular_spectrum(full, pb.k, g.L, d, g.n_max, eps0)[n:]
+            err = max(err, rel_l2(rows[q * planes + j - 1], ref))
+    return err
+
+
+def pin_linear_ray_steps(O, nt=8):
+    """Rays of eps = 1 + a z stopped after k of nt RK4 steps against their
+    closed form at x = k dx / nt (the state and amplitude on a plane inside
+    the screen)."""
+    a, dx = 0.01, 20.0
+    pb = _linear_problem(a, dx, nt)
+    o = O(pb)
+    kap = np.array([-0.3, 0.0, 0.4])
+    s = np.array([-5.0, 10.0, 33.0])
+    err = 0.0
+    for k in (1, nt // 2, nt - 1):
+        got = o.march(0, kap, s, steps=k)
+        for i in range(len(kap)):
+            ref = linear_ray(kap[i], s[i], a, dx * k / nt)
+            for key, scale in (("z", abs(ref["z"] - s[i]) + 1.0), ("Q", 1.0),
+                               ("r", abs(ref["r"])), ("Zs", 1.0)):
+                err = max(err, abs(got[key][i] - ref[key]) / scale)
+            err = max(err, abs(got["a"][i] - 1.0 / math.sqrt(ref["Zs"])))
+    return err
+
+
+def pin_planes_before_absorber(O, planes=4):
+    """With a top absorber, the planes inside the first screen still carry
+    the unabsorbed field: plane j equals the angular spectrum of u0 over
+    j dx / planes (the absorber acts only on screens)."""
+    pb = w.config_homogeneous(eps0=1.0, n_z=128, height=32.0, dx=15.0, n_screens=1,
+                              ray_stride=1, rk4_steps=8).with_(absorber_frac=0.3)
+    o = O(pb)
+    rows = o.propagate_planes(pb.u0, 0, 1, planes)
+    g = o.g
+    err = 0.0
+    for j in range(1, planes):
+        ref = angular_spectrum(pb.u0, pb.k, g.L, j * pb.dx / planes, g.n_max, 1.0)
+        err = max(err, rel_l2(rows[j - 1], ref))
+    return err

@@ -12,17 +12,28 @@ from oracle.swkb_oracle import Oracle
 
 
 class NoSqrtAmplitude(Oracle):            # paper's printed A = (J/J0) A0 form
-    def march(self, q, kappa, s):
-        r = super().march(q, kappa, s)
+    def march(self, q, kappa, s, steps=None):
+        r = super().march(q, kappa, s, steps)
         r["a"] = r["a"] ** 2
         return r
 
 
 class SwappedP0P1(Oracle):
-    def march(self, q, kappa, s):
-        r = super().march(q, kappa, s)
+    def march(self, q, kappa, s, steps=None):
+        r = super().march(q, kappa, s, steps)
         r["a"] = np.sqrt(r["P1"] / (r["P0"] * r["Zs"]))
         return r
+
+
+class PlanesMarchWholeScreen(Oracle):     # planes reuse the screen's landing
+    def march(self, q, kappa, s, steps=None):
+        return super().march(q, kappa, s)
+
+
+class PlanesWithAbsorber(Oracle):         # absorber applied between screens too
+    def screen_planes(self, u, q, planes):
+        return [f * self.W for f in super().screen_planes(u, q, planes)[:-1]] + \
+            super().screen_planes(u, q, planes)[-1:]
 
 
 def _rhs_variant(kind):
@@ -79,6 +90,10 @@ def _caught(O):
         lambda: P.pin_tube_flux(O) > 1e-6,
         lambda: P.pin_tube_flux(O, x_dependent=True) > 1e-6,
         lambda: P.pin_interp_stencil(O) > 1e-9,
+        lambda: P.pin_planes_homogeneous(O) > 1e-12,
+        lambda: P.pin_planes_homogeneous(O, bc=1) > 1e-12,
+        lambda: P.pin_linear_ray_steps(O) > 1e-7,
+        lambda: P.pin_planes_before_absorber(O) > 1e-12,
     ]
     for c in checks:
         try:
@@ -92,9 +107,10 @@ def _caught(O):
 @pytest.mark.parametrize("O", [NoSqrtAmplitude, SwappedP0P1, _rhs_variant("dQ-factor"),
                                _rhs_variant("dr-kappa2"), _rhs_variant("Ps-sign"),
                                _rhs_variant("Qs-drop"), ConjugateDFT, ShiftedOrigin,
-                               ShiftedStencil],
+                               ShiftedStencil, PlanesMarchWholeScreen, PlanesWithAbsorber],
                          ids=["amp-no-sqrt", "P0-P1-swap", "dQ-factor", "dr-kappa2", "Ps-sign",
-                              "Qs-drop", "conj-dft", "origin-shift", "stencil-shift"])
+                              "Qs-drop", "conj-dft", "origin-shift", "stencil-shift",
+                              "planes-whole-screen", "planes-absorbed"])
 def test_planted_mistake_is_caught(O):
     assert _caught(O)
 

@@ -139,3 +139,26 @@ def test_sampled_screen_equals_full_screen():
     ms = [o.g.N // 2, o.g.N // 2 + 7, o.g.N - 40, 3 * o.g.N // 4 + 123, 100]
     got = o.screen_points(u, 2, ms)
     assert np.max(np.abs(got - full[ms])) < 1e-12 * np.max(np.abs(full))
+
+
+@pytest.mark.parametrize("bc", [w.BC_PERIODIC, w.BC_NEUMANN, w.BC_DIRICHLET])
+def test_planes_between_screens_homogeneous(bc):
+    assert P.pin_planes_homogeneous(Oracle, bc) < 1e-12
+
+
+def test_linear_ray_stopped_inside_the_screen():
+    assert P.pin_linear_ray_steps(Oracle) < 1e-7
+
+
+def test_last_plane_is_the_screen():
+    pb = w.config_surface_duct_small(n_screens=2, n_z=1024, height=20.0)
+    o = Oracle(pb)
+    rows = o.propagate_planes(pb.u0, 0, 2, 4)
+    _, snaps = o.propagate(pb.u0, 0, 2, snapshots=True)
+    assert np.array_equal(rows[3], snaps[0]) and np.array_equal(rows[7], snaps[1])
+    with pytest.raises(ValueError):
+        o.screen_planes(o.extend(pb.u0), 0, 3)
+
+
+def test_planes_inside_a_screen_carry_no_absorber():
+    assert P.pin_planes_before_absorber(Oracle) < 1e-12
