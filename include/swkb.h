@@ -117,6 +117,10 @@ typedef struct {
                              depend only on the medium slab, not on the
                              field, so results are identical (0 = march every
                              screen, the default)                             */
+  int32_t planes;         /* P > 1 (dividing rk4_steps): allocate ray buffers
+                             for P - 1 planes inside each screen, enabling
+                             swkb_propagate_planes with up to P planes per
+                             screen (0 or 1 = none)                           */
 } swkb_options;
 
 typedef struct {
@@ -168,6 +172,25 @@ swkb_status swkb_plan_get_info(const swkb_plan* plan, swkb_plan_info* info);
  */
 swkb_status swkb_propagate(swkb_plan* plan, const double* u0, int32_t q0, int32_t n_screens,
                            double* u_out, int32_t snapshot_every, int32_t on_device);
+
+/*
+ * Fields between screens (Sec. 2.1: further interpolation points may be
+ * added for visualisation).  Like swkb_propagate, but u_out receives
+ * n_screens * planes fields of n_z complex128 values, rows ordered (screen,
+ * plane): row (q - q0) planes + j - 1 is the field on x_q + j dx / planes,
+ * j = 1..planes.  The last row of each screen is the screen's field (the
+ * snapshot swkb_propagate returns, absorber applied); the rows before it are
+ * the ray field inside the screen: the screen's modes, its rays stopped after
+ * j rk4_steps / planes RK4 steps, interpolated and summed like the screen,
+ * with the range phase of that plane and no absorber.  planes must divide
+ * rk4_steps and be at most the plan's swkb_options.planes (1 always works).
+ * Pointers and blocking as in swkb_propagate; runs without a CUDA graph.
+ * Errors: SWKB_ERR_INVALID_ARG (NULL, counts, planes), the ray statuses of
+ * swkb_propagate.
+ */
+swkb_status swkb_propagate_planes(swkb_plan* plan, const double* u0, int32_t q0,
+                                  int32_t n_screens, int32_t planes, double* u_out,
+                                  int32_t on_device);
 
 /*
  * One screen with every intermediate exposed, for testing (host pointers;

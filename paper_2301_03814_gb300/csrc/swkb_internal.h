@@ -65,6 +65,13 @@ struct MarchArgs {
   T* out_d;         // [NRT][Mr] landing offset from the launch grid point, grid units
   T* out_ph;        // [NRT][Mr] residual phase k (r - x P_bar) / (2 pi), turns
   T* out_a;         // [NRT][Mr] amplitude factor sqrt(P0 / (P1 Z_s))
+  // fields between screens: after every plane_steps RK4 steps (before the
+  // last) the same three quantities go to plane j = steps / plane_steps - 1
+  // of pl_d / pl_ph / pl_a, [planes - 1][NRT][Mr]; plane_steps = 0: none
+  int plane_steps;
+  T* pl_d;
+  T* pl_ph;
+  T* pl_a;
   unsigned* status;
 };
 
@@ -132,6 +139,10 @@ template <typename T> cudaError_t launch_bracket(const BracketArgs<T>& a, cudaSt
 template <typename T> cudaError_t launch_resum(const ResumArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_output(const typename C2<T>::type* u, int offset, int n,
                                                 double* out, cudaStream_t s);
+template <typename T> cudaError_t launch_cscale(const typename C2<T>::type* c,
+                                                const typename C2<T>::type* f,
+                                                typename C2<T>::type* out, int M,
+                                                cudaStream_t s);
 template <typename T> size_t resum_smem_bytes(int wcap, int tile_points);
 // Raise the dynamic shared-memory limit of the resummation kernels
 // on the current device (call once per device before launching).

@@ -199,7 +199,7 @@ __device__ __forceinline__ Ray<T> axpy(const Ray<T>& y, T a, const Ray<T>& k) {
 
 // Block (32, 8): lanes are 32 consecutive modes at one launch height, so a
 // warp's table reads stay within a few z-intervals; warps are 8 rays.
-template <typename T, bool MULTI>
+template <typename T, bool MULTI, bool PLANES>
 __global__ void __launch_bounds__(256) k_march(const MarchArgs<T> p) {
   const int r = blockIdx.x * 32 + threadIdx.x;       // marched mode (output column)
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -215,6 +215,19 @@ __global__ void __launch_bounds__(256) k_march(const MarchArgs<T> p) {
   const T P0 = sqrt(P0sq);
   Ray<T> y{T(0), T(0), T(0), T(1), T(0)};
   const T h = p.h, hh = T(0.5) * p.h, h6 = p.h / T(6);
+  // landing quantities at RK4 stage l (the screen's end, or a plane inside it)
+  auto land = [&](int l, T* od, T* oph, T* oa) {
+    const long long o = (long long)j * p.Mr + r;
+    if (!(y.Zs > T(0))) st |= ST_CAUSTIC;
+    T e1, ez1, ezz1;
+    medium_eval<T, MULTI>(p, l, s + y.dz, e1, ez1, ezz1, st);
+    T P1sq = pb2 + e1 - y.dQ * (T(2) * kap + y.dQ);
+    if (!(P1sq > T(0))) { st |= ST_TURNING; P1sq = pb2; }
+    const T Zs = y.Zs > T(0) ? y.Zs : T(1);
+    od[o] = y.dz * p.inv_dz;
+    oph[o] = y.rh * p.k_over_2pi;
+    oa[o] = sqrt(P0 * rsqrt_t(P1sq) / Zs);
+  };
   for (int n = 0; n < p.Nt; ++n) {
     const Ray<T> k1 = rhs<T, MULTI>(p, 2 * n, s, kap, pb, pb2, y, st);
     const Ray<T> k2 = rhs<T, MULTI>(p, 2 * n + 1, s, kap, pb, pb2, axpy(y, hh, k1), st);
@@ -225,22 +238,18 @@ __global__ void __launch_bounds__(256) k_march(const MarchArgs<T> p) {
     y.rh += h6 * (k1.rh + T(2) * k2.rh + T(2) * k3.rh + k4.rh);
     y.Zs += h6 * (k1.Zs + T(2) * k2.Zs + T(2) * k3.Zs + k4.Zs);
     y.Qs += h6 * (k1.Qs + T(2) * k2.Qs + T(2) * k3.Qs + k4.Qs);
+    if (PLANES && (n + 1) % p.plane_steps == 0 && n + 1 < p.Nt) {
+      const long long po = (long long)((n + 1) / p.plane_steps - 1) * p.NRT * p.Mr;
+      land(2 * (n + 1), p.pl_d + po, p.pl_ph + po, p.pl_a + po);
+    }
   }
-  if (!(y.Zs > T(0))) st |= ST_CAUSTIC;
-  medium_eval<T, MULTI>(p, 2 * p.Nt, s + y.dz, e, ez, ezz, st);
-  T P1sq = pb2 + e - y.dQ * (T(2) * kap + y.dQ);
-  if (!(P1sq > T(0))) { st |= ST_TURNING; P1sq = pb2; }
-  const T Zs = y.Zs > T(0) ? y.Zs : T(1);
-  const long long o = (long long)j * p.Mr + r;
-  p.out_d[o] = y.dz * p.inv_dz;
-  p.out_ph[o] = y.rh * p.k_over_2pi;
-  p.out_a[o] = sqrt(P0 * rsqrt_t(P1sq) / Zs);
+  land(2 * p.Nt, p.out_d, p.out_ph, p.out_a);
   if (st) atomicOr(p.status, st);
 }
 
 // ----------------------------------------------------------------------------
 // (b) ray march, FP32 path with packed f32x2 arithmetic: each thread marches
-// two rays (j and j + 8 of one mode).  The medium lookups stay per ray; the
+// two rays of one mode (see k_march_x2 for which).  The medium lookups stay per ray; the
 // right-hand side of the ray + variational system and the RK4 updates run on
 // register pairs, halving their issue slots (same IEEE round-to-nearest
 // operations as the scalar kernel, in the same order up to FMA contraction).
@@ -380,7 +389,7 @@ __device__ __forceinline__ Ray2 axpy2(const Ray2& y, f2 a, const Ray2& k) {
 // Thread t marches rays q and q + NH of mode r, t = q Mr + r (NH = ceil(NRT / 2)):
 // a warp's lanes are consecutive modes at one launch height (their table
 // reads stay within a few intervals) and no lane idles at the end of a row.
-template <bool MULTI>
+template <bool MULTI, bool PLANES>
 __global__ void __launch_bounds__(256) k_march_x2(const MarchArgs<float> p) {
   const int NH = (p.NRT + 1) >> 1;
   const int t = blockIdx.x * 256 + threadIdx.x;
@@ -413,6 +422,33 @@ __global__ void __launch_bounds__(256) k_march_x2(const MarchArgs<float> p) {
   const f2 h = bc2(p.h), hh = bc2(0.5f * p.h), h6 = bc2(p.h / 6.f);
   // table position of a ray: launch position + dz / h_table
   const auto pos = [&](const Ray2& w) { return fma2(w.dz, ih, s); };
+  // landing quantities at RK4 stage l (the screen's end, or a plane inside it)
+  const auto land = [&](int l, float* od, float* oph, float* oam) {
+    const long long oa = (long long)ja * p.Mr + r, ob = (long long)jb * p.Mr + r;
+    float dza, dzb, dQa, dQb, rha, rhb, Zsa, Zsb, u1a, u1b;
+    sp2(y.dz, dza, dzb);
+    sp2(y.dQ, dQa, dQb);
+    sp2(y.rh, rha, rhb);
+    sp2(y.Zs, Zsa, Zsb);
+    sp2(pos(y), u1a, u1b);
+    if (!(Zsa > 0.f) || !(Zsb > 0.f)) st |= ST_CAUSTIC;
+    float e1a, e1b, s0, s1;
+    med32<MULTI>(p, l, u1a, e1a, s0, s1, st);
+    med32<MULTI>(p, l, u1b, e1b, s0, s1, st);
+    float P1a = pb2 + e1a - dQa * (2.f * kap + dQa);
+    float P1b = pb2 + e1b - dQb * (2.f * kap + dQb);
+    if (!(P1a > 0.f)) { st |= ST_TURNING; P1a = pb2; }
+    if (!(P1b > 0.f)) { st |= ST_TURNING; P1b = pb2; }
+    const float Za = Zsa > 0.f ? Zsa : 1.f, Zb = Zsb > 0.f ? Zsb : 1.f;
+    od[oa] = dza * p.inv_dz;
+    oph[oa] = rha * p.k_over_2pi;
+    oam[oa] = sqrtf(P0a * rsqrtf(P1a) / Za);
+    if (has_b) {
+      od[ob] = dzb * p.inv_dz;
+      oph[ob] = rhb * p.k_over_2pi;
+      oam[ob] = sqrtf(P0b * rsqrtf(P1b) / Zb);
+    }
+  };
   // RK4: y + h/6 k1 + h/3 k2 + h/3 k3 + h/6 k4, accumulated as the stages
   // complete (k1..k3 need not stay live)
   const f2 h3 = bc2(p.h / 3.f);
@@ -432,32 +468,12 @@ __global__ void __launch_bounds__(256) k_march_x2(const MarchArgs<float> p) {
     const Ray2 k4 = rhs2<MULTI>(p, 2 * n + 2, pos(y4), kv, m2kap, mkap, pbv, mpb, pb2, pb2v,
                                 ihh, mihh, ihq, y4, st);
     y = axpy2(acc, h6, k4);
+    if (PLANES && (n + 1) % p.plane_steps == 0 && n + 1 < p.Nt) {
+      const long long po = (long long)((n + 1) / p.plane_steps - 1) * p.NRT * p.Mr;
+      land(2 * (n + 1), p.pl_d + po, p.pl_ph + po, p.pl_a + po);
+    }
   }
-  float dza, dzb, dQa, dQb, rha, rhb, Zsa, Zsb, u1a, u1b;
-  sp2(y.dz, dza, dzb);
-  sp2(y.dQ, dQa, dQb);
-  sp2(y.rh, rha, rhb);
-  sp2(y.Zs, Zsa, Zsb);
-  sp2(pos(y), u1a, u1b);
-  if (!(Zsa > 0.f) || !(Zsb > 0.f)) st |= ST_CAUSTIC;
-  float e1a, e1b;
-  med32<MULTI>(p, 2 * p.Nt, u1a, e1a, t0, t1, st);
-  med32<MULTI>(p, 2 * p.Nt, u1b, e1b, t0, t1, st);
-  float P1a = pb2 + e1a - dQa * (2.f * kap + dQa);
-  float P1b = pb2 + e1b - dQb * (2.f * kap + dQb);
-  if (!(P1a > 0.f)) { st |= ST_TURNING; P1a = pb2; }
-  if (!(P1b > 0.f)) { st |= ST_TURNING; P1b = pb2; }
-  const float Za = Zsa > 0.f ? Zsa : 1.f, Zb = Zsb > 0.f ? Zsb : 1.f;
-  const long long oa = (long long)ja * p.Mr + r;
-  p.out_d[oa] = dza * p.inv_dz;
-  p.out_ph[oa] = rha * p.k_over_2pi;
-  p.out_a[oa] = sqrtf(P0a * rsqrtf(P1a) / Za);
-  if (has_b) {
-    const long long ob = (long long)jb * p.Mr + r;
-    p.out_d[ob] = dzb * p.inv_dz;
-    p.out_ph[ob] = rhb * p.k_over_2pi;
-    p.out_a[ob] = sqrtf(P0b * rsqrtf(P1b) / Zb);
-  }
+  land(2 * p.Nt, p.out_d, p.out_ph, p.out_a);
   if (st) atomicOr(p.status, st);
 }
 
@@ -1000,6 +1016,15 @@ __global__ void __launch_bounds__(256) k_fft1(const FftArgs<T> p) {
   }
 }
 
+// out_i = c_i f_i (mode coefficients of a plane between screens).
+template <typename T>
+__global__ void k_cscale(const typename C2<T>::type* __restrict__ c,
+                         const typename C2<T>::type* __restrict__ f,
+                         typename C2<T>::type* __restrict__ out, int M) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < M) out[i] = cmul<T>(c[i], f[i]);
+}
+
 // w_{N2}^{idx} from the table of w_N (w_{N2} = w_N^{N1}).
 template <typename V>
 __device__ __forceinline__ V twiddle2(const V* tw, unsigned idx, int, int N1) {
@@ -1110,16 +1135,22 @@ template <typename T>
 cudaError_t launch_march(const MarchArgs<T>& a, bool multi_column, cudaStream_t s) {
   dim3 block(32, 8);
   dim3 grid((a.Mr + 31) / 32, (a.NRT + 7) / 8);
-  return multi_column ? launch_k(k_march<T, true>, grid, block, 0, s, a)
-                      : launch_k(k_march<T, false>, grid, block, 0, s, a);
+  if (a.plane_steps > 0)
+    return multi_column ? launch_k(k_march<T, true, true>, grid, block, 0, s, a)
+                        : launch_k(k_march<T, false, true>, grid, block, 0, s, a);
+  return multi_column ? launch_k(k_march<T, true, false>, grid, block, 0, s, a)
+                      : launch_k(k_march<T, false, false>, grid, block, 0, s, a);
 }
 
 template <>
 cudaError_t launch_march<float>(const MarchArgs<float>& a, bool multi_column, cudaStream_t s) {
   const long long threads = (long long)a.Mr * ((a.NRT + 1) / 2);
   const dim3 block(256), grid((unsigned)((threads + 255) / 256));
-  return multi_column ? launch_k(k_march_x2<true>, grid, block, 0, s, a)
-                      : launch_k(k_march_x2<false>, grid, block, 0, s, a);
+  if (a.plane_steps > 0)
+    return multi_column ? launch_k(k_march_x2<true, true>, grid, block, 0, s, a)
+                        : launch_k(k_march_x2<false, true>, grid, block, 0, s, a);
+  return multi_column ? launch_k(k_march_x2<true, false>, grid, block, 0, s, a)
+                      : launch_k(k_march_x2<false, false>, grid, block, 0, s, a);
 }
 
 template <typename T>
@@ -1177,6 +1208,12 @@ cudaError_t prepare_fft_kernels() {
 }
 
 template <typename T>
+cudaError_t launch_cscale(const typename C2<T>::type* c, const typename C2<T>::type* f,
+                          typename C2<T>::type* out, int M, cudaStream_t s) {
+  return launch_k(k_cscale<T>, dim3((M + 255) / 256), dim3(256), 0, s, c, f, out, M);
+}
+
+template <typename T>
 cudaError_t launch_output(const typename C2<T>::type* u, int offset, int n, double* out,
                           cudaStream_t s) {
   return launch_k(k_output<T>, dim3((n + 255) / 256), dim3(256), 0, s, u, offset, n, out);
@@ -1190,6 +1227,8 @@ cudaError_t launch_output(const typename C2<T>::type* u, int offset, int n, doub
   template cudaError_t launch_bracket<T>(const BracketArgs<T>&, cudaStream_t);                  \
   template cudaError_t launch_resum<T>(const ResumArgs<T>&, cudaStream_t);                      \
   template cudaError_t launch_output<T>(const C2<T>::type*, int, int, double*, cudaStream_t);   \
+  template cudaError_t launch_cscale<T>(const C2<T>::type*, const C2<T>::type*, C2<T>::type*,   \
+                                        int, cudaStream_t);                                     \
   template size_t resum_smem_bytes<T>(int, int);                                                \
   template cudaError_t prepare_kernels<T>(int);                                                 \
   template cudaError_t prepare_fft_kernels<T>();

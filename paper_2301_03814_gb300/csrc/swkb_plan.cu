@@ -106,6 +106,14 @@ struct swkb_plan {
   void* rd = nullptr;
   void* rph = nullptr;
   void* ra = nullptr;
+  // fields between screens: ray data of planes - 1 inner planes, the mode
+  // coefficients of one plane, its range-phase factors
+  int planes = 0;
+  void* pl_d = nullptr;
+  void* pl_ph = nullptr;
+  void* pl_a = nullptr;
+  void* c_plane = nullptr;
+  void* ephi_pl = nullptr;
   int* jlo = nullptr;
   int* jlo_neg = nullptr;
   unsigned* status = nullptr;
@@ -325,6 +333,14 @@ swkb_status build_device(swkb_plan* p, const swkb_profile* prof) {
   TRY(dev_alloc(p, &p->rd, rays * sizeof(T)));
   TRY(dev_alloc(p, &p->rph, rays * sizeof(T)));
   TRY(dev_alloc(p, &p->ra, rays * sizeof(T)));
+  if (p->planes > 1) {
+    const size_t pr = (size_t)(p->planes - 1) * rays;
+    TRY(dev_alloc(p, &p->pl_d, pr * sizeof(T)));
+    TRY(dev_alloc(p, &p->pl_ph, pr * sizeof(T)));
+    TRY(dev_alloc(p, &p->pl_a, pr * sizeof(T)));
+    TRY(dev_alloc(p, &p->c_plane, (size_t)M * sizeof(V)));
+    TRY(dev_alloc(p, &p->ephi_pl, (size_t)(p->planes - 1) * M * sizeof(V)));
+  }
   const size_t jn = (size_t)(p->alloc_tiles + 1) * p->Mr;
   TRY(dev_alloc(p, (void**)&p->jlo, jn * sizeof(int)));
   CK(cudaMemsetAsync(p->jlo, 0, jn * sizeof(int), p->stream));
@@ -426,8 +442,32 @@ MarchArgs<T> march_args(const swkb_plan* p, int q) {
   a.h = (T)(p->dx / p->Nt);
   a.k_over_2pi = (T)(p->k / (2.0 * M_PI));
   a.out_d = (T*)p->rd; a.out_ph = (T*)p->rph; a.out_a = (T*)p->ra;
+  a.plane_steps = 0;
+  a.pl_d = a.pl_ph = a.pl_a = nullptr;
   a.status = p->status;
   return a;
+}
+
+template <typename T>
+BracketArgs<T> bracket_args(const swkb_plan* p, const T* d) {
+  return BracketArgs<T>{d, p->Mr, p->NRT, p->G, p->R, p->N, p->TM, p->n_tiles,
+                        p->jlo, p->sym, p->jlo_neg, p->status};
+}
+
+template <typename T>
+ResumArgs<T> resum_args(const swkb_plan* p, const T* d, const T* ph, const T* a,
+                        const typename C2<T>::type* c) {
+  using V = typename C2<T>::type;
+  ResumArgs<T> ra;
+  ra.d = d; ra.ph = ph; ra.a = a; ra.jlo = p->jlo;
+  ra.jlo_neg = p->jlo_neg;
+  ra.c = c;
+  ra.M = p->M; ra.Mr = p->Mr; ra.sym = p->sym; ra.n_tiles_run = p->n_tiles_run; ra.NRT = p->NRT;
+  ra.G = p->G; ra.R = p->R; ra.N = p->N; ra.TM = p->TM;
+  ra.PW = p->PW; ra.n_tiles = p->n_tiles; ra.n_groups = p->n_groups;
+  ra.modes_per_group = p->modes_per_group; ra.n_max = p->n_max; ra.wcap = p->wcap;
+  ra.part = (V*)p->part; ra.status = p->status;
+  return ra;
 }
 
 template <typename T>
@@ -459,18 +499,11 @@ swkb_status launch_screen(swkb_plan* p, int q, bool u_fresh) {
   const bool march = !(p->reuse_rays && p->rays_ready);
   if (march)
     TRY(timed(p, SWKB_KERNEL_MARCH, 1, [&] { return launch_march<T>(ma, multi, s); }));
-  BracketArgs<T> b{(const T*)p->rd, p->Mr, p->NRT, p->G, p->R, p->N, p->TM, p->n_tiles,
-                   p->jlo, p->sym, p->jlo_neg, p->status};
+  const BracketArgs<T> b = bracket_args<T>(p, (const T*)p->rd);
   if (march) TRY(timed(p, SWKB_KERNEL_BRACKET, 1, [&] { return launch_bracket<T>(b, s); }));
   p->rays_ready = true;
-  ResumArgs<T> ra;
-  ra.d = (const T*)p->rd; ra.ph = (const T*)p->rph; ra.a = (const T*)p->ra; ra.jlo = p->jlo;
-  ra.jlo_neg = p->jlo_neg;
-  ra.c = (const V*)p->c;
-  ra.M = p->M; ra.Mr = p->Mr; ra.sym = p->sym; ra.n_tiles_run = p->n_tiles_run; ra.NRT = p->NRT; ra.G = p->G; ra.R = p->R; ra.N = p->N; ra.TM = p->TM;
-  ra.PW = p->PW; ra.n_tiles = p->n_tiles; ra.n_groups = p->n_groups;
-  ra.modes_per_group = p->modes_per_group; ra.n_max = p->n_max; ra.wcap = p->wcap;
-  ra.part = (V*)p->part; ra.status = p->status;
+  const ResumArgs<T> ra = resum_args<T>(p, (const T*)p->rd, (const T*)p->rph, (const T*)p->ra,
+                                        (const V*)p->c);
   TRY(timed(p, SWKB_KERNEL_RESUM, 1, [&] { return launch_resum<T>(ra, s); }));
   p->stats.screens += 1;
   return SWKB_OK;
@@ -536,6 +569,104 @@ swkb_status enqueue(swkb_plan* p, const double* u0, int q0, int n, double* out_d
     if (!fresh) TRY(reduce_to_u<T>(p, true));
     TRY(emit(0));
   }
+  return SWKB_OK;
+}
+
+// Fields on the planes x_q + j dx / P (j = 1..P) of screens q0 .. q0 + n - 1,
+// rows ordered (screen, plane); the last plane of a screen is the screen's
+// field, the planes before it are the ray field between screens: the
+// screen's modes, its rays stopped after j N_t / P RK4 steps, the same
+// interpolation and sum with the range-phase carry of that plane, and no
+// absorber.  Uses the inner-plane buffers (P <= the plan's planes option).
+template <typename T>
+swkb_status enqueue_planes(swkb_plan* p, const double* u0, int q0, int n, int P,
+                           double* out_dev, double* out_host) {
+  using V = typename C2<T>::type;
+  cudaStream_t s = p->stream;
+  p->rays_ready = false;
+  const int off = p->mirror ? p->n_z : 0;
+  const size_t nb = 2 * sizeof(double) * p->n_z;
+  const size_t rays = (size_t)p->NRT * p->Mr;
+  TRY(timed(p, SWKB_KERNEL_INIT, 1,
+            [&] { return launch_init<T>(u0, p->n_z, p->N, p->mirror, (V*)p->u, s); }));
+  int row = 0;
+  auto emit = [&]() -> swkb_status {
+    const int idx = row++;
+    double* dst = out_dev ? out_dev + 2 * (size_t)idx * p->n_z : p->io;
+    TRY(timed(p, SWKB_KERNEL_OUTPUT, 1,
+              [&] { return launch_output<T>((const V*)p->u, off, p->n_z, dst, s); }));
+    if (!out_dev)
+      CK(cudaMemcpyAsync(out_host + 2 * (size_t)idx * p->n_z, p->io, nb, cudaMemcpyDeviceToHost,
+                         s));
+    return SWKB_OK;
+  };
+  // partials -> field on the whole period (grounded: reflection fill), with
+  // or without the absorber
+  auto reduce = [&](const T* W) -> swkb_status {
+    ReduceArgs<T> r{(const V*)p->part, p->n_groups, p->N, W, p->mirror, p->sym, (V*)p->u};
+    TRY(timed(p, SWKB_KERNEL_REDUCE, 1, [&] { return launch_reduce<T>(r, s); }));
+    return SWKB_OK;
+  };
+  for (int q = q0; q < q0 + n; ++q) {
+    FftArgs<T> f;
+    f.u = (const V*)p->u; f.tw = (const V*)p->tw; f.Y = (V*)p->Y;
+    f.N = p->N; f.N1 = p->N1; f.N2 = p->N2; f.log2N2 = p->log2N2; f.n_max = p->n_max;
+    f.mirror = p->mirror;
+    f.part = nullptr;
+    f.n_part = p->n_groups;
+    f.sym = p->sym;
+    f.W = (const T*)p->W;
+    f.inv_N = (T)(1.0 / p->N);
+    f.ephi = (const V*)p->ephi_d; f.c = (V*)p->c;
+    TRY(timed(p, SWKB_KERNEL_FFT, p->N1 > 1 ? 2 : 1, [&] { return launch_fft<T>(f, s); }));
+    MarchArgs<T> ma = march_args<T>(p, q);
+    if (P > 1) {
+      ma.plane_steps = p->Nt / P;
+      ma.pl_d = (T*)p->pl_d; ma.pl_ph = (T*)p->pl_ph; ma.pl_a = (T*)p->pl_a;
+    }
+    const bool multi = p->n_cols > 1;
+    TRY(timed(p, SWKB_KERNEL_MARCH, 1, [&] { return launch_march<T>(ma, multi, s); }));
+    for (int j = 1; j < P; ++j) {
+      const size_t o = (size_t)(j - 1) * rays;
+      const BracketArgs<T> b = bracket_args<T>(p, (const T*)p->pl_d + o);
+      TRY(timed(p, SWKB_KERNEL_BRACKET, 1, [&] { return launch_bracket<T>(b, s); }));
+      // c_n of plane j: the screen's c_n (carried over dx) times exp(i k (j/P - 1) dx P_bar_n)
+      const V* fj = (const V*)p->ephi_pl + (size_t)(j - 1) * p->M;
+      TRY(timed(p, SWKB_KERNEL_REDUCE, 1, [&] {
+        return launch_cscale<T>((const V*)p->c, fj, (V*)p->c_plane, p->M, s);
+      }));
+      const ResumArgs<T> ra = resum_args<T>(p, (const T*)p->pl_d + o, (const T*)p->pl_ph + o,
+                                            (const T*)p->pl_a + o, (const V*)p->c_plane);
+      TRY(timed(p, SWKB_KERNEL_RESUM, 1, [&] { return launch_resum<T>(ra, s); }));
+      TRY(reduce(nullptr));
+      TRY(emit());
+    }
+    const BracketArgs<T> b = bracket_args<T>(p, (const T*)p->rd);
+    TRY(timed(p, SWKB_KERNEL_BRACKET, 1, [&] { return launch_bracket<T>(b, s); }));
+    const ResumArgs<T> ra = resum_args<T>(p, (const T*)p->rd, (const T*)p->rph, (const T*)p->ra,
+                                          (const V*)p->c);
+    TRY(timed(p, SWKB_KERNEL_RESUM, 1, [&] { return launch_resum<T>(ra, s); }));
+    TRY(reduce((const T*)p->W));
+    TRY(emit());
+    p->stats.screens += 1;
+  }
+  return SWKB_OK;
+}
+
+// Range-phase factors exp(i k (j/P - 1) dx P_bar_n) of the inner planes
+// j = 1..P-1, formed in FP64 and reduced mod 2 pi on the host.
+template <typename T>
+swkb_status upload_plane_phases(swkb_plan* p, int P) {
+  std::vector<T> f(2 * (size_t)(P - 1) * p->M);
+  for (int j = 1; j < P; ++j)
+    for (int i = 0; i < p->M; ++i) {
+      const double phi = fmod(p->k * p->dx * ((double)j / P - 1.0) * p->pbar[i], 2.0 * M_PI);
+      f[2 * ((size_t)(j - 1) * p->M + i)] = (T)cos(phi);
+      f[2 * ((size_t)(j - 1) * p->M + i) + 1] = (T)sin(phi);
+    }
+  CK(cudaMemcpyAsync(p->ephi_pl, f.data(), f.size() * sizeof(T), cudaMemcpyHostToDevice,
+                     p->stream));
+  CK(cudaStreamSynchronize(p->stream));
   return SWKB_OK;
 }
 
@@ -707,6 +838,8 @@ void swkb_options_default(swkb_options* o) {
   o->autotune = 0;
   o->cuda_stream = nullptr;
   o->device = 0;
+  o->reuse_rays = 0;
+  o->planes = 0;
 }
 
 const char* swkb_last_error(void) { return g_err.c_str(); }
@@ -890,6 +1023,9 @@ swkb_status configure(swkb_plan* p, const swkb_profile* prof, double k, const sw
   CK(cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device));
   p->autotune = opt.autotune != 0;
   p->reuse_rays = opt.reuse_rays != 0 && p->n_cols == 1;
+  p->planes = opt.planes > 1 ? opt.planes : 0;
+  if (p->planes && (p->planes > p->Nt || p->Nt % p->planes))
+    return fail(SWKB_ERR_INVALID_ARG, "planes (%d) must divide rk4_steps (%d)", p->planes, p->Nt);
   const Tiling def = default_tiling(p);
   apply_tiling(p, def);
   p->alloc_groups = p->n_groups;
@@ -916,6 +1052,9 @@ size_t device_bytes(const swkb_plan* p) {
   if (p->absorber_frac > 0) b += (size_t)p->N * T;                  // absorber
   b += (size_t)p->N * V * (2 + (size_t)p->alloc_groups) + (size_t)p->M * V;  // u, Y, partials, c
   b += 3 * (size_t)p->NRT * p->Mr * T;                              // rays
+  if (p->planes > 1)                                                 // inner planes
+    b += (size_t)(p->planes - 1) * (3 * (size_t)p->NRT * p->Mr * T + (size_t)p->M * V) +
+         (size_t)p->M * V;
   b += (size_t)(p->alloc_tiles + 1) * p->Mr * sizeof(int) * (p->sym ? 2 : 1);
   b += 16 + 2 * (size_t)std::max(p->N, p->n_z) * sizeof(double);   // status, io
   return b;
@@ -1160,6 +1299,38 @@ swkb_status swkb_propagate(swkb_plan* p, const double* u0, int32_t q0, int32_t n
     return p->precision == SWKB_FP64
                ? run<double>(p, din, q0, n_screens, odev, ohost, snapshot_every)
                : run<float>(p, din, q0, n_screens, odev, ohost, snapshot_every);
+  } catch (...) {
+    return fail(SWKB_ERR_INVALID_ARG, "unexpected exception");
+  }
+}
+
+swkb_status swkb_propagate_planes(swkb_plan* p, const double* u0, int32_t q0, int32_t n_screens,
+                                  int32_t planes, double* u_out, int32_t on_device) {
+  try {
+    if (!p || !u0 || !u_out) return fail(SWKB_ERR_INVALID_ARG, "NULL argument");
+    if (n_screens < 0 || q0 < 0) return fail(SWKB_ERR_INVALID_ARG, "negative screen count");
+    if (planes < 1 || p->Nt % planes)
+      return fail(SWKB_ERR_INVALID_ARG, "planes (%d) must divide rk4_steps (%d)", planes, p->Nt);
+    if (planes > std::max(1, p->planes))
+      return fail(SWKB_ERR_INVALID_ARG,
+                  "plan holds buffers for %d planes per screen (swkb_options.planes)",
+                  std::max(1, p->planes));
+    CK(cudaSetDevice(p->device));
+    if (n_screens == 0) return SWKB_OK;
+    const bool f64 = p->precision == SWKB_FP64;
+    if (planes > 1) TRY(f64 ? upload_plane_phases<double>(p, planes)
+                            : upload_plane_phases<float>(p, planes));
+    const size_t nb = 2 * sizeof(double) * p->n_z;
+    const double* din = u0;
+    if (!on_device) {
+      CK(cudaMemcpyAsync(p->io, u0, nb, cudaMemcpyHostToDevice, p->stream));
+      din = p->io;   // consumed by the init kernel before any output reuses io
+    }
+    double* odev = on_device ? u_out : nullptr;
+    double* ohost = on_device ? nullptr : u_out;
+    TRY(f64 ? enqueue_planes<double>(p, din, q0, n_screens, planes, odev, ohost)
+            : enqueue_planes<float>(p, din, q0, n_screens, planes, odev, ohost));
+    return read_status(p);
   } catch (...) {
     return fail(SWKB_ERR_INVALID_ARG, "unexpected exception");
   }

@@ -35,7 +35,7 @@ SWKB_FP64, SWKB_MIXED = 0, 1
 KERNEL_KINDS = ("init", "reduce", "fft", "march", "bracket", "resum", "output")
 
 EXPORTED = ("swkb_options_default", "swkb_plan_create", "swkb_plan_get_info", "swkb_propagate",
-            "swkb_debug_screen", "swkb_plan_destroy", "swkb_plan_set_timing",
+            "swkb_propagate_planes", "swkb_debug_screen", "swkb_plan_destroy", "swkb_plan_set_timing",
             "swkb_plan_get_stats", "swkb_server_create", "swkb_submit",
             "swkb_poll", "swkb_cancel", "swkb_server_get_stats", "swkb_server_destroy",
             "swkb_last_error", "swkb_status_string", "swkb_modes_noalloc")
@@ -61,7 +61,7 @@ class swkb_options(ctypes.Structure):
     _fields_ = [("precision", c_int32), ("theta_max", c_double), ("n_max", c_int32),
                 ("ray_stride", c_int32), ("rk4_steps", c_int32), ("absorber_frac", c_double),
                 ("autotune", c_int32), ("cuda_stream", c_void_p), ("device", c_int32),
-                ("reuse_rays", c_int32)]
+                ("reuse_rays", c_int32), ("planes", c_int32)]
 
 
 class swkb_plan_info(ctypes.Structure):
@@ -109,6 +109,8 @@ def lib():
         L.swkb_plan_get_info.argtypes = [c_void_p, POINTER(swkb_plan_info)]
         L.swkb_propagate.argtypes = [c_void_p, c_void_p, c_int32, c_int32, c_void_p, c_int32,
                                      c_int32]
+        L.swkb_propagate_planes.argtypes = [c_void_p, c_void_p, c_int32, c_int32, c_int32,
+                                            c_void_p, c_int32]
         L.swkb_debug_screen.argtypes = [c_void_p, c_int32] + [c_void_p] * 6
         L.swkb_plan_set_timing.argtypes = [c_void_p, c_int32, c_int32]
         L.swkb_plan_get_stats.argtypes = [c_void_p, POINTER(swkb_plan_stats)]
@@ -180,7 +182,7 @@ def swkb_options_default() -> swkb_options:
 
 
 def options_for(problem, precision=SWKB_FP64, stream=None, device=0, autotune=False,
-                reuse_rays=False) -> swkb_options:
+                reuse_rays=False, planes=0) -> swkb_options:
     o = swkb_options_default()
     o.precision = precision
     o.theta_max = float(problem.theta_max)
@@ -192,6 +194,7 @@ def options_for(problem, precision=SWKB_FP64, stream=None, device=0, autotune=Fa
     o.device = device
     o.autotune = 1 if autotune else 0
     o.reuse_rays = 1 if reuse_rays else 0
+    o.planes = int(planes)
     return o
 
 
@@ -218,6 +221,16 @@ def swkb_propagate(plan, u0, q0, n_screens, u_out, snapshot_every=0, on_device=0
                                           c_void_p(int(u_out)), snapshot_every, 1))
     return check(lib().swkb_propagate(plan, u0.ctypes.data_as(c_void_p), q0, n_screens,
                                       u_out.ctypes.data_as(c_void_p), snapshot_every, 0))
+
+
+def swkb_propagate_planes(plan, u0, q0, n_screens, planes, u_out, on_device=0):
+    """Fields on `planes` planes per screen (rows ordered (screen, plane));
+    u0 / u_out as in swkb_propagate."""
+    if on_device:
+        return check(lib().swkb_propagate_planes(plan, c_void_p(int(u0)), q0, n_screens, planes,
+                                                 c_void_p(int(u_out)), 1))
+    return check(lib().swkb_propagate_planes(plan, u0.ctypes.data_as(c_void_p), q0, n_screens,
+                                             planes, u_out.ctypes.data_as(c_void_p), 0))
 
 
 def swkb_plan_destroy(plan):
@@ -350,10 +363,11 @@ class Plan:
     """A plan for one workloads.Problem (or equivalent fields)."""
 
     def __init__(self, problem, precision=SWKB_FP64, stream=None, device=0, autotune=False,
-                 reuse_rays=False):
+                 reuse_rays=False, planes=0):
         self.problem = problem
         dom = swkb_domain(problem.z_a, problem.z_b, problem.x0, problem.bc)
-        self.options = options_for(problem, precision, stream, device, autotune, reuse_rays)
+        self.options = options_for(problem, precision, stream, device, autotune, reuse_rays,
+                                   planes)
         self.handle = swkb_plan_create(problem.profile, problem.k, dom, problem.n_z,
                                        problem.dx, self.options)
         self.info = swkb_plan_get_info(self.handle)
@@ -386,6 +400,23 @@ class Plan:
         if n_screens is None:
             n_screens = self.problem.n_screens
         return swkb_propagate(self.handle, u0_ptr, q0, n_screens, out_ptr, snapshot_every, 1)
+
+    def propagate_planes(self, planes, u0=None, q0=0, n_screens=None):
+        """Host arrays: (n_screens * planes, n_z) complex128 fields, rows
+        ordered (screen, plane), the last of each screen being its field."""
+        if u0 is None:
+            u0 = self.problem.u0
+        if n_screens is None:
+            n_screens = self.problem.n_screens
+        u0 = np.ascontiguousarray(u0, dtype=np.complex128)
+        out = np.empty(n_screens * planes * self.n_z, dtype=np.complex128)
+        swkb_propagate_planes(self.handle, u0, q0, n_screens, planes, out, 0)
+        return out.reshape(n_screens * planes, self.n_z)
+
+    def propagate_planes_device(self, planes, u0_ptr: int, out_ptr: int, q0=0, n_screens=None):
+        if n_screens is None:
+            n_screens = self.problem.n_screens
+        return swkb_propagate_planes(self.handle, u0_ptr, q0, n_screens, planes, out_ptr, 1)
 
     def set_timing(self, kinds=True, every=1):
         swkb_plan_set_timing(self.handle, kinds, every)

@@ -47,8 +47,35 @@ def test_status_strings_and_defaults(built):
     assert o.precision == swkb.SWKB_FP64 and o.ray_stride == 1 and o.rk4_steps == 8
 
 
-def test_struct_layouts_match_header():
-    # sizes of the C structs as laid out by a C compiler for this ABI (LP64)
-    assert ctypes.sizeof(swkb.swkb_domain) == 32
-    assert ctypes.sizeof(swkb.swkb_profile) == 64
-    assert ctypes.sizeof(swkb.swkb_options) == 64
+STRUCTS = ("swkb_profile", "swkb_domain", "swkb_options", "swkb_plan_info", "swkb_plan_stats",
+           "swkb_request", "swkb_server_stats")
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """Every ctypes mirror has the C compiler's size and field offsets: a C
+    program built against include/swkb.h prints them (a field name missing
+    from the header fails to compile)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "swkb.h"', "int main(void) {"]
+    for name in STRUCTS:
+        st = getattr(swkb, name)
+        lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        for f in st._fields_:
+            lines.append(f'  printf("{name}.{f[0]} %zu\\n", offsetof({name}, {f[0]}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                 text=True).stdout.splitlines())
+    for name in STRUCTS:
+        st = getattr(swkb, name)
+        assert int(got[name]) == ctypes.sizeof(st), name
+        for f in st._fields_:
+            assert int(got[f"{name}.{f[0]}"]) == getattr(st, f[0]).offset, (name, f[0])
