@@ -56,3 +56,33 @@ def airy_field(u0, z, k, a, x, zeta):
         A = c * c * (Ai @ u0) * dz
         out += (A * np.exp(1j * beta[i0:i0 + chunk] * x)) @ Ai * dzeta
     return out
+
+
+def hill_one_way(u0, k, L, eps, x, K, n_quad=4096):
+    """Separation-of-variables solution (Sec. 3.1, Eqs. series_sol,
+    phi_equation, series_init, sl_expansion) for an x-invariant permittivity
+    periodic on the period of the field samples u0 (N samples over length L);
+    eps is a callable of the offset t in [0, L) from the first sample.
+
+    The Sturm-Liouville problem phi'' + k^2 eps phi = alpha^2 phi with
+    periodic conditions is discretised by Fourier-Galerkin on the modes
+    |n| <= K (the Hill matrix H_nm = -(2 pi n / L)^2 delta_nm + k^2 eps^_(n-m),
+    eps^_j the Fourier coefficients of eps); H is Hermitian, so its
+    eigenvectors are orthonormal and the expansion coefficients of u0 are
+    plain projections.  Each eigen-mode advances by exp(i alpha x), alpha =
+    sqrt(lambda) (decaying for lambda < 0).  Returns u(x) on the same grid."""
+    N = len(u0)
+    t = L * np.arange(n_quad) / n_quad
+    eh = np.fft.fft(eps(t)) / n_quad                      # eps^_j, j mod n_quad
+    n = np.arange(-K, K + 1)
+    j = (n[:, None] - n[None, :]) % n_quad
+    H = k * k * eh[j]
+    H[np.diag_indices_from(H)] += -(2.0 * math.pi * n / L) ** 2
+    lam, V = np.linalg.eigh(H)
+    alpha = np.sqrt(lam.astype(np.complex128))
+    uh = np.fft.fft(u0) / N                               # u0 = sum_n uh_n e^{2 pi i n m / N}
+    c = V.conj().T @ uh[n % N]
+    vh = V @ (c * np.exp(1j * alpha * x))
+    out_h = np.zeros(N, dtype=np.complex128)
+    out_h[n % N] = vh
+    return np.fft.ifft(out_h) * N
