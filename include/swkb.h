@@ -139,6 +139,9 @@ typedef struct {
   double dz, period;      /* grid spacing, period length                      */
   double eps_ref;         /* reference permittivity of the phase carry        */
   size_t device_bytes;    /* device memory held by the plan                   */
+  int32_t medium_pieces;  /* FP32 plans: cubic pieces per permittivity-table
+                             interval the march evaluates (0: the quintic
+                             itself; always 0 for FP64 plans)                 */
 } swkb_plan_info;
 
 /* Fill *opt with defaults: FP64, theta_max 30 deg, R 1, N_t 8, no absorber. */

@@ -30,7 +30,10 @@ template <> struct C2<double> { using type = double2; };
 //   mirror images of the n_int intervals below z_a, then the n_int intervals
 //   above), followed by one interval continuing the last one, so that a
 //   position exactly at the top has a t = 0 entry; n_int counts the intervals
-//   before that pad and top = n_int as a float.
+//   before that pad and top = n_int as a float.  When pieces = S > 0 every
+//   interval is stored as S cubic Hermite pieces of its quintic (value and
+//   slope matched at the piece ends; 4 slots b0..b3 in the piece's own
+//   tau in [0, 1]) and n_int, top, inv_h, inv_h2 count pieces.
 template <typename T>
 struct Medium {
   const T* coef;
@@ -40,6 +43,7 @@ struct Medium {
   int mirrored;
   T z_mirror;
   T top;
+  int pieces;   // FP32: > 0 when each entry is a cubic piece (4 slots), in piece units
 };
 
 // Per-screen RK4 stage columns: stage l = 0 .. 2 N_t sits at x_q + l h / 2;

@@ -310,28 +310,50 @@ __device__ __forceinline__ void horner5(const float* q, float t, float& e, float
   e = b; d1 = c1; d2 = c2;
 }
 
-template <bool MULTI>
+// Cubic piece b0..b3 in tau (one 16-byte load): value, first derivative and
+// half the second derivative by synthetic division (6 FMAs).
+__device__ __forceinline__ void horner3(const float* q, float t, float& e, float& d1, float& d2) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(q));
+  float b = v.w * t + v.z;
+  float c1 = v.w * t + b;
+  b = b * t + v.y;
+  const float c2 = v.w * t + c1;
+  c1 = c1 * t + b;
+  b = b * t + v.x;
+  e = b; d1 = c1; d2 = c2;
+}
+
+template <bool CUBIC>
+__device__ __forceinline__ void table_eval(const float* q, float t, float& e, float& d1,
+                                           float& d2) {
+  if (CUBIC) horner3(q, t, e, d1, d2);
+  else horner5(q, t, e, d1, d2);
+}
+
+// CUBIC: the table holds cubic pieces (4 slots each, u in piece units).
+template <bool MULTI, bool CUBIC>
 __device__ __forceinline__ void med32(const MarchArgs<float>& p, int l, float u, float& e,
                                       float& d1, float& d2, unsigned& st) {
+  constexpr int W = CUBIC ? 4 : 8;
   const float uc = fminf(fmaxf(u, 0.f), p.med.top);
   if (uc != u) st |= ST_RANGE;
   const float v = __fadd_rd(uc, 12582912.f);
   const int i = (int)(__float_as_uint(v) - 0x4B400000u);
   const float t = uc - (v - 12582912.f);
   if (!MULTI) {
-    horner5(p.med.coef + (long long)i * 8, t, e, d1, d2);
+    table_eval<CUBIC>(p.med.coef + (long long)i * W, t, e, d1, d2);
   } else {
     const int c = __ldg(p.st.c + l);
     const float th = __ldg(p.st.th + l);
-    const float* q = p.med.coef + (long long)c * p.med.col_stride + (long long)i * 8;
+    const float* q = p.med.coef + (long long)c * p.med.col_stride + (long long)i * W;
     if (th == 0.f) {
-      horner5(q, t, e, d1, d2);
+      table_eval<CUBIC>(q, t, e, d1, d2);
     } else if (th == 1.f) {
-      horner5(q + p.med.col_stride, t, e, d1, d2);
+      table_eval<CUBIC>(q + p.med.col_stride, t, e, d1, d2);
     } else {
       float e0, e1, f0, f1, g0, g1;
-      horner5(q, t, e0, f0, g0);
-      horner5(q + p.med.col_stride, t, e1, f1, g1);
+      table_eval<CUBIC>(q, t, e0, f0, g0);
+      table_eval<CUBIC>(q + p.med.col_stride, t, e1, f1, g1);
       e = (1.f - th) * e0 + th * e1;
       d1 = (1.f - th) * f0 + th * f1;
       d2 = (1.f - th) * g0 + th * g1;
@@ -344,15 +366,15 @@ __device__ __forceinline__ void med32(const MarchArgs<float>& p, int l, float u,
 // 1 / h^2):  z' = Q/P,  Q' = he/P,  r' - P_bar as in the scalar kernel,
 //   -P_s/P = (Q Q_s - he Z_s)/P^2,  Z_s' = (Q_s + Q (-P_s/P))/P,
 //   Q_s' = (hee Z_s + he (-P_s/P))/P.
-template <bool MULTI>
+template <bool MULTI, bool CUBIC>
 __device__ __forceinline__ Ray2 rhs2(const MarchArgs<float>& p, int l, f2 u2, f2 kap, f2 m2kap,
                                      f2 mkap, f2 pb, f2 mpb, float pb2, f2 pb2v, f2 ihh,
                                      f2 mihh, f2 ihq, const Ray2& y, unsigned& st) {
   float ua, ub;
   sp2(u2, ua, ub);
   float ea, d1a, d2a, eb, d1b, d2b;
-  med32<MULTI>(p, l, ua, ea, d1a, d2a, st);
-  med32<MULTI>(p, l, ub, eb, d1b, d2b, st);
+  med32<MULTI, CUBIC>(p, l, ua, ea, d1a, d2a, st);
+  med32<MULTI, CUBIC>(p, l, ub, eb, d1b, d2b, st);
   const f2 e = mk2(ea, eb), d1 = mk2(d1a, d1b);
   const f2 he = mul2(d1, ihh), mhe = mul2(d1, mihh), hee = mul2(mk2(d2a, d2b), ihq);
   const f2 Q = add2(kap, y.dQ);
@@ -389,7 +411,7 @@ __device__ __forceinline__ Ray2 axpy2(const Ray2& y, f2 a, const Ray2& k) {
 // Thread t marches rays q and q + NH of mode r, t = q Mr + r (NH = ceil(NRT / 2)):
 // a warp's lanes are consecutive modes at one launch height (their table
 // reads stay within a few intervals) and no lane idles at the end of a row.
-template <bool MULTI, bool PLANES>
+template <bool MULTI, bool PLANES, bool CUBIC>
 __global__ void __launch_bounds__(256) k_march_x2(const MarchArgs<float> p) {
   const int NH = (p.NRT + 1) >> 1;
   const int t = blockIdx.x * 256 + threadIdx.x;
@@ -410,8 +432,8 @@ __global__ void __launch_bounds__(256) k_march_x2(const MarchArgs<float> p) {
   const f2 ih = bc2(ihs), ihh = bc2(0.5f * ihs), mihh = bc2(-0.5f * ihs);
   const f2 ihq = bc2(0.5f * p.med.inv_h2);   // inv_h2 = 2 / h^2
   float e0a, e0b, t0, t1;
-  med32<MULTI>(p, 0, ua, e0a, t0, t1, st);
-  med32<MULTI>(p, 0, ub, e0b, t0, t1, st);
+  med32<MULTI, CUBIC>(p, 0, ua, e0a, t0, t1, st);
+  med32<MULTI, CUBIC>(p, 0, ub, e0b, t0, t1, st);
   float P0a = pb2 + e0a, P0b = pb2 + e0b;
   if (!(P0a > 0.f)) { st |= ST_TURNING; P0a = pb2; }
   if (!(P0b > 0.f)) { st |= ST_TURNING; P0b = pb2; }
@@ -433,8 +455,8 @@ __global__ void __launch_bounds__(256) k_march_x2(const MarchArgs<float> p) {
     sp2(pos(y), u1a, u1b);
     if (!(Zsa > 0.f) || !(Zsb > 0.f)) st |= ST_CAUSTIC;
     float e1a, e1b, s0, s1;
-    med32<MULTI>(p, l, u1a, e1a, s0, s1, st);
-    med32<MULTI>(p, l, u1b, e1b, s0, s1, st);
+    med32<MULTI, CUBIC>(p, l, u1a, e1a, s0, s1, st);
+    med32<MULTI, CUBIC>(p, l, u1b, e1b, s0, s1, st);
     float P1a = pb2 + e1a - dQa * (2.f * kap + dQa);
     float P1b = pb2 + e1b - dQb * (2.f * kap + dQb);
     if (!(P1a > 0.f)) { st |= ST_TURNING; P1a = pb2; }
@@ -453,19 +475,19 @@ __global__ void __launch_bounds__(256) k_march_x2(const MarchArgs<float> p) {
   // complete (k1..k3 need not stay live)
   const f2 h3 = bc2(p.h / 3.f);
   for (int n = 0; n < p.Nt; ++n) {
-    const Ray2 k1 = rhs2<MULTI>(p, 2 * n, pos(y), kv, m2kap, mkap, pbv, mpb, pb2, pb2v, ihh,
+    const Ray2 k1 = rhs2<MULTI, CUBIC>(p, 2 * n, pos(y), kv, m2kap, mkap, pbv, mpb, pb2, pb2v, ihh,
                                 mihh, ihq, y, st);
     Ray2 acc = axpy2(y, h6, k1);
     const Ray2 y2 = axpy2(y, hh, k1);
-    const Ray2 k2 = rhs2<MULTI>(p, 2 * n + 1, pos(y2), kv, m2kap, mkap, pbv, mpb, pb2, pb2v,
+    const Ray2 k2 = rhs2<MULTI, CUBIC>(p, 2 * n + 1, pos(y2), kv, m2kap, mkap, pbv, mpb, pb2, pb2v,
                                 ihh, mihh, ihq, y2, st);
     acc = axpy2(acc, h3, k2);
     const Ray2 y3 = axpy2(y, hh, k2);
-    const Ray2 k3 = rhs2<MULTI>(p, 2 * n + 1, pos(y3), kv, m2kap, mkap, pbv, mpb, pb2, pb2v,
+    const Ray2 k3 = rhs2<MULTI, CUBIC>(p, 2 * n + 1, pos(y3), kv, m2kap, mkap, pbv, mpb, pb2, pb2v,
                                 ihh, mihh, ihq, y3, st);
     acc = axpy2(acc, h3, k3);
     const Ray2 y4 = axpy2(y, h, k3);
-    const Ray2 k4 = rhs2<MULTI>(p, 2 * n + 2, pos(y4), kv, m2kap, mkap, pbv, mpb, pb2, pb2v,
+    const Ray2 k4 = rhs2<MULTI, CUBIC>(p, 2 * n + 2, pos(y4), kv, m2kap, mkap, pbv, mpb, pb2, pb2v,
                                 ihh, mihh, ihq, y4, st);
     y = axpy2(acc, h6, k4);
     if (PLANES && (n + 1) % p.plane_steps == 0 && n + 1 < p.Nt) {
@@ -1146,11 +1168,19 @@ template <>
 cudaError_t launch_march<float>(const MarchArgs<float>& a, bool multi_column, cudaStream_t s) {
   const long long threads = (long long)a.Mr * ((a.NRT + 1) / 2);
   const dim3 block(256), grid((unsigned)((threads + 255) / 256));
-  if (a.plane_steps > 0)
-    return multi_column ? launch_k(k_march_x2<true, true>, grid, block, 0, s, a)
-                        : launch_k(k_march_x2<false, true>, grid, block, 0, s, a);
-  return multi_column ? launch_k(k_march_x2<true, false>, grid, block, 0, s, a)
-                      : launch_k(k_march_x2<false, false>, grid, block, 0, s, a);
+  const bool pl = a.plane_steps > 0, cub = a.med.pieces > 0;
+  if (cub) {
+    if (pl)
+      return multi_column ? launch_k(k_march_x2<true, true, true>, grid, block, 0, s, a)
+                          : launch_k(k_march_x2<false, true, true>, grid, block, 0, s, a);
+    return multi_column ? launch_k(k_march_x2<true, false, true>, grid, block, 0, s, a)
+                        : launch_k(k_march_x2<false, false, true>, grid, block, 0, s, a);
+  }
+  if (pl)
+    return multi_column ? launch_k(k_march_x2<true, true, false>, grid, block, 0, s, a)
+                        : launch_k(k_march_x2<false, true, false>, grid, block, 0, s, a);
+  return multi_column ? launch_k(k_march_x2<true, false, false>, grid, block, 0, s, a)
+                      : launch_k(k_march_x2<false, false, false>, grid, block, 0, s, a);
 }
 
 template <typename T>

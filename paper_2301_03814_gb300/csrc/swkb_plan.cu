@@ -80,6 +80,7 @@ struct swkb_plan {
   int alloc_groups = 0, alloc_tiles = 0;   // buffer sizes: max over tuning candidates
   // medium
   int n_cols = 0, n_p = 0, n_int = 0;
+  int pieces = 0;   // FP32: cubic pieces per table interval (0: the quintic)
   double z0p = 0, dzp = 0;
   std::vector<double> x_cols;
   int stage_rows = 1;  // screens q >= stage_rows - 1 share the last row
@@ -200,31 +201,106 @@ swkb_status status_from_bits(unsigned bits) {
 // Intervals of the FP32 medium table of one column (layout in swkb_internal.h).
 int table32_intervals(const swkb_plan* p) { return (p->mirror ? 2 : 1) * p->n_int + 1; }
 
+// Quintic Hermite interpolant of eps - eps_ref on every profile interval, as
+// monomial coefficients a0..a5 in t in [0, 1] (8 slots per interval).
+std::vector<double> quintic_coefficients(const swkb_plan* p, const swkb_profile* prof) {
+  std::vector<double> coef((size_t)p->n_cols * p->n_int * 8, 0.0);
+  const double h = p->dzp;
+  for (int c = 0; c < p->n_cols; ++c) {
+    const double* e = prof->eps + (size_t)c * p->n_p;
+    const double* ez = prof->eps_z + (size_t)c * p->n_p;
+    const double* ezz = prof->eps_zz + (size_t)c * p->n_p;
+    for (int i = 0; i < p->n_int; ++i) {
+      const double f0 = e[i] - p->eps_ref, f1 = e[i + 1] - p->eps_ref;
+      const double a0 = f0, a1 = h * ez[i], a2 = 0.5 * h * h * ezz[i];
+      const double A = f1 - a0 - a1 - a2;
+      const double B = h * ez[i + 1] - a1 - 2.0 * a2;
+      const double C = h * h * ezz[i + 1] - 2.0 * a2;
+      double* o = coef.data() + ((size_t)c * p->n_int + i) * 8;
+      o[0] = a0; o[1] = a1; o[2] = a2;
+      o[3] = 10.0 * A - 4.0 * B + 0.5 * C;
+      o[4] = -15.0 * A + 7.0 * B - C;
+      o[5] = 6.0 * A - 3.0 * B + 0.5 * C;
+    }
+  }
+  return coef;
+}
+
+// value, first and second t-derivative of a quintic at t
+void quintic_eval(const double* a, double t, double& v, double& d1, double& d2) {
+  v = ((((a[5] * t + a[4]) * t + a[3]) * t + a[2]) * t + a[1]) * t + a[0];
+  d1 = (((5.0 * a[5] * t + 4.0 * a[4]) * t + 3.0 * a[3]) * t + 2.0 * a[2]) * t + a[1];
+  d2 = ((20.0 * a[5] * t + 12.0 * a[4]) * t + 6.0 * a[3]) * t + 2.0 * a[2];
+}
+
+// Cubic Hermite piece s of S of a quintic (value and slope matched at both
+// ends), as monomial coefficients b0..b3 in tau in [0, 1].
+void cubic_piece(const double* a, int s, int S, double* b) {
+  double f0, d0, g0, f1, d1, g1;
+  quintic_eval(a, (double)s / S, f0, d0, g0);
+  quintic_eval(a, (double)(s + 1) / S, f1, d1, g1);
+  d0 /= S; d1 /= S;                                  // d/dtau = (1/S) d/dt
+  b[0] = f0;
+  b[1] = d0;
+  b[2] = 3.0 * (f1 - f0) - 2.0 * d0 - d1;
+  b[3] = 2.0 * (f0 - f1) + d0 + d1;
+}
+
+// FP32 plans evaluate each interval's quintic through S cubic Hermite pieces
+// (6 FMAs per lookup instead of 12).  S is the smallest of 1, 2, 4, 8, 16 for
+// which, at the quarter points of every piece, value, slope and curvature of
+// the pieces stay within 1e-7, 1e-6 and 1e-4 of the table's largest |e|, |e_z|
+// and |e_zz| (e = eps - eps_ref): far below what the FP32 march resolves.
+// 0 when none does (the quintic itself is evaluated).
+int choose_pieces(const swkb_plan* p, const std::vector<double>& coef) {
+  const double h = p->dzp;
+  const size_t n = (size_t)p->n_cols * p->n_int;
+  double E0 = 0, E1 = 0, E2 = 0;
+  for (size_t i = 0; i < n; ++i) {
+    const double* a = coef.data() + i * 8;
+    for (double t : {0.0, 1.0}) {
+      double v, d1, d2;
+      quintic_eval(a, t, v, d1, d2);
+      E0 = std::max(E0, fabs(v));
+      E1 = std::max(E1, fabs(d1) / h);
+      E2 = std::max(E2, fabs(d2) / (h * h));
+    }
+  }
+  const long long ext = (long long)(p->mirror ? 2 : 1) * p->n_int;
+  for (int S = 1; S <= 16; S *= 2) {
+    if (ext * S >= (1LL << 22)) break;            // FP32 positions stay exact below 2^22
+    bool ok = true;
+    for (size_t i = 0; i < n && ok; ++i) {
+      const double* a = coef.data() + i * 8;
+      for (int s = 0; s < S && ok; ++s) {
+        double b[4];
+        cubic_piece(a, s, S, b);
+        for (double tau : {0.25, 0.5, 0.75}) {
+          double v, d1, d2;
+          quintic_eval(a, (s + tau) / S, v, d1, d2);
+          const double cv = ((b[3] * tau + b[2]) * tau + b[1]) * tau + b[0];
+          const double c1 = ((3.0 * b[3] * tau + 2.0 * b[2]) * tau + b[1]) * S;
+          const double c2 = (6.0 * b[3] * tau + 2.0 * b[2]) * S * S;
+          if (fabs(cv - v) > 1e-7 * E0 || fabs(c1 - d1) / h > 1e-6 * E1 ||
+              fabs(c2 - d2) / (h * h) > 1e-4 * E2) {
+            ok = false;
+            break;
+          }
+        }
+      }
+    }
+    if (ok) return S;
+  }
+  return 0;
+}
+
 template <typename T>
 swkb_status build_device(swkb_plan* p, const swkb_profile* prof) {
   using V = typename C2<T>::type;
   const int M = p->M, N = p->N;
   // medium coefficient table (eps - eps_ref), 8 slots per interval
   {
-    std::vector<double> coef((size_t)p->n_cols * p->n_int * 8, 0.0);
-    const double h = p->dzp;
-    for (int c = 0; c < p->n_cols; ++c) {
-      const double* e = prof->eps + (size_t)c * p->n_p;
-      const double* ez = prof->eps_z + (size_t)c * p->n_p;
-      const double* ezz = prof->eps_zz + (size_t)c * p->n_p;
-      for (int i = 0; i < p->n_int; ++i) {
-        const double f0 = e[i] - p->eps_ref, f1 = e[i + 1] - p->eps_ref;
-        const double a0 = f0, a1 = h * ez[i], a2 = 0.5 * h * h * ezz[i];
-        const double A = f1 - a0 - a1 - a2;
-        const double B = h * ez[i + 1] - a1 - 2.0 * a2;
-        const double C = h * h * ezz[i + 1] - 2.0 * a2;
-        double* o = coef.data() + ((size_t)c * p->n_int + i) * 8;
-        o[0] = a0; o[1] = a1; o[2] = a2;
-        o[3] = 10.0 * A - 4.0 * B + 0.5 * C;
-        o[4] = -15.0 * A + 7.0 * B - C;
-        o[5] = 6.0 * A - 3.0 * B + 0.5 * C;
-      }
-    }
+    const std::vector<double> coef = quintic_coefficients(p, prof);
     if (sizeof(T) == 8) {
       TRY(upload<T>(p, &p->coef, coef));
     } else {
@@ -254,7 +330,16 @@ swkb_status build_device(swkb_plan* p, const swkb_profile* prof) {
             }
           }
         }
-      TRY(upload<T>(p, &p->coef, c32));
+      if (p->pieces > 0) {
+        // cubic pieces, 4 floats each, S per extended interval
+        const int S = p->pieces;
+        std::vector<double> cub((size_t)p->n_cols * nt * S * 4);
+        for (size_t k = 0; k < (size_t)p->n_cols * nt; ++k)
+          for (int sp = 0; sp < S; ++sp) cubic_piece(c32.data() + k * 8, sp, S, &cub[(k * S + sp) * 4]);
+        TRY(upload<T>(p, &p->coef, cub));
+      } else {
+        TRY(upload<T>(p, &p->coef, c32));
+      }
     }
   }
   // RK4 stage columns for screens 0 .. stage_rows - 1
@@ -416,16 +501,23 @@ MarchArgs<T> march_args(const swkb_plan* p, int q) {
   a.med.mirrored = p->mirror != 0;
   a.med.z_mirror = (T)p->z_a;
   a.med.top = (T)p->n_int;
+  a.med.pieces = 0;
   if (sizeof(T) == 4) {
     // reflection stored in the table; positions in table intervals
     const double z0 = p->mirror ? p->z0p - p->n_int * p->dzp : p->z0p;
-    a.med.n_int = (p->mirror ? 2 : 1) * p->n_int;
-    a.med.col_stride = (long long)table32_intervals(p) * 8;
+    // with cubic pieces, positions and derivatives are in piece units
+    const int S = p->pieces > 0 ? p->pieces : 1;
+    const double hs = p->dzp / S;
+    a.med.n_int = (p->mirror ? 2 : 1) * p->n_int * S;
+    a.med.col_stride = (long long)table32_intervals(p) * (p->pieces > 0 ? 4 * S : 8);
     a.med.z0 = (T)z0;
+    a.med.inv_h = (T)(1.0 / hs);
+    a.med.inv_h2 = (T)(2.0 / (hs * hs));
     a.med.mirrored = 0;
+    a.med.pieces = p->pieces;
     a.med.top = (T)a.med.n_int;
-    a.u_lo = (T)((p->z_lo - z0) / p->dzp);
-    a.u_dz = (T)(p->dz / p->dzp);
+    a.u_lo = (T)((p->z_lo - z0) / hs);
+    a.u_dz = (T)(p->dz / hs);
   } else {
     a.u_lo = a.u_dz = T(0);
   }
@@ -1010,6 +1102,7 @@ swkb_status configure(swkb_plan* p, const swkb_profile* prof, double k, const sw
     if (!(p->eps_ref - kmax * kmax > 0))
       return fail(SWKB_ERR_INVALID_ARG, "steepest kept mode is evanescent at eps_ref");
   }
+  p->pieces = p->precision == SWKB_FP64 ? 0 : choose_pieces(p, quintic_coefficients(p, prof));
   if (p->n_cols > 1) {
     const double q_end = ceil((p->x_cols.back() - p->x0) / p->dx);
     p->stage_rows = (int)std::min(std::max(q_end, 0.0), 1e6) + 1;
@@ -1045,7 +1138,9 @@ swkb_status configure(swkb_plan* p, const swkb_profile* prof, double k, const sw
 size_t device_bytes(const swkb_plan* p) {
   const size_t T = p->precision == SWKB_FP64 ? 8 : 4, V = 2 * T;
   const size_t S = 2 * (size_t)p->Nt + 1;
-  size_t b = (size_t)p->n_cols * (T == 8 ? p->n_int : table32_intervals(p)) * 8 * T;  // medium
+  size_t b = (size_t)p->n_cols * (T == 8 ? (size_t)p->n_int * 8                      // medium
+                                          : (size_t)table32_intervals(p) *
+                                                (p->pieces > 0 ? 4 * p->pieces : 8)) * T;
   b += (size_t)p->stage_rows * S * (sizeof(int) + T);               // stage columns
   b += 3 * (size_t)p->M * T + (size_t)p->M * V;                     // mode tables
   b += (size_t)p->N * V;                                            // twiddles
@@ -1271,6 +1366,7 @@ swkb_status swkb_plan_get_info(const swkb_plan* p, swkb_plan_info* info) {
   info->period = p->L;
   info->eps_ref = p->eps_ref;
   info->device_bytes = p->bytes;
+  info->medium_pieces = p->pieces;
   return SWKB_OK;
 }
 

@@ -69,7 +69,8 @@ class swkb_plan_info(ctypes.Structure):
                 ("n_rays", c_int32), ("n_ghost", c_int32), ("n_rays_total", c_int32),
                 ("tile_points", c_int32), ("mode_groups", c_int32), ("march_modes", c_int32),
                 ("resum_points", c_int32), ("fft_n1", c_int32), ("dz", c_double),
-                ("period", c_double), ("eps_ref", c_double), ("device_bytes", c_size_t)]
+                ("period", c_double), ("eps_ref", c_double), ("device_bytes", c_size_t),
+                ("medium_pieces", c_int32)]
 
 
 class swkb_plan_stats(ctypes.Structure):

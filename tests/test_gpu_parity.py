@@ -295,3 +295,13 @@ def test_reuse_rays_identical_for_range_independent_media(prec):
     c1 = w.config_unit_periodic(n_screens=6)
     assert np.array_equal(swkb.Plan(c1, prec, reuse_rays=True).propagate(),
                           swkb.Plan(c1, prec).propagate())
+
+
+def test_fp32_medium_pieces():
+    # FP32 plans evaluate the quintic table through cubic pieces: one per
+    # interval where the profile is smooth on the table scale, 16 for the
+    # duct (its 1 m blends set the curvature criterion), none in FP64
+    duct = duct_small()
+    assert swkb.Plan(duct, swkb.SWKB_MIXED).info.medium_pieces == 16
+    assert swkb.Plan(duct, swkb.SWKB_FP64).info.medium_pieces == 0
+    assert swkb.Plan(w.config_gaussian_medium(), swkb.SWKB_MIXED).info.medium_pieces == 1
