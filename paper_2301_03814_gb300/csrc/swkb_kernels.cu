@@ -38,9 +38,6 @@ namespace swkb {
 // ----------------------------------------------------------------------------
 // small helpers
 // ----------------------------------------------------------------------------
-__device__ __forceinline__ void sincospi_t(float x, float* s, float* c) { sincospif(x, s, c); }
-__device__ __forceinline__ void sincospi_t(double x, double* s, double* c) { sincospi(x, s, c); }
-
 // sin / cos of 2 pi t for |t| <= 1/2: the FP32 path uses the special-function
 // unit (absolute error ~2^-21 on [-pi, pi]); the FP64 path stays exact.
 __device__ __forceinline__ void sincos_turns(float t, float* s, float* c) {
