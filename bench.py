@@ -56,6 +56,9 @@ def parse_args():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="default launch shapes instead of the autotuned ones (for profiling)")
+    ap.add_argument("--large", action="store_true",
+                    help="instead of the benchmark, time the paper-scale range-dependent duct "
+                         "and the full uneven batch once (one JSON line; minutes)")
     return ap.parse_args()
 
 
@@ -502,11 +505,62 @@ def run_ours(args, world, rank, local):
     return 0
 
 
+def run_large():
+    """One-off full-size runs, host wall clock around a device synchronisation:
+    the paper-scale range-dependent duct (500 m, N_z = 131072, 100 km, 2000
+    screens, 101 table columns) mixed and autotuned, its first 100 screens in
+    FP64 and mixed (rel-L2 between them), and the 64-instance uneven batch
+    (full ranges) through the request server."""
+    import torch
+    from paper_2301_03814_gb300 import swkb
+    from paper_2301_03814_gb300 import workloads as w
+    out = {"impl": "ours", "large_runs": {}}
+    pb = w.config_range_dependent_duct()
+    u0 = torch.from_numpy(pb.u0).cuda()
+    res = {}
+    for prec, name in ((swkb.SWKB_MIXED, "mixed"), (swkb.SWKB_FP64, "fp64")):
+        plan = swkb.Plan(pb, prec, autotune=(prec == swkb.SWKB_MIXED))
+        dst = torch.empty_like(u0)
+        n = pb.n_screens if prec == swkb.SWKB_MIXED else 100
+        plan.propagate_device(u0.data_ptr(), dst.data_ptr(), n_screens=min(n, 4))   # warm-up
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        plan.propagate_device(u0.data_ptr(), dst.data_ptr(), n_screens=n)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        out["large_runs"][f"paper_scale_{name}"] = {
+            "screens": n, "seconds": dt, "screen_points_per_s": pb.n_z * n / dt,
+            "medium_pieces": int(plan.info.medium_pieces)}
+        if prec == swkb.SWKB_MIXED:
+            d100 = torch.empty_like(u0)
+            plan.propagate_device(u0.data_ptr(), d100.data_ptr(), n_screens=100)
+            res["mixed"] = d100.cpu().numpy()
+        else:
+            res["fp64"] = dst.cpu().numpy()
+        plan.close()
+    out["large_runs"]["paper_scale_mixed_vs_fp64_100_screens"] = rel_l2(res["mixed"], res["fp64"])
+    batch = w.batch_uneven(4, 64)
+    srv = swkb.Server(96 << 30, max_slots=16)
+    t = time.perf_counter()
+    tickets = [srv.submit(b, swkb.SWKB_MIXED)[1] for b in batch]
+    sts = [srv.poll(tk, timeout_ms=-1)[0] for tk in tickets]
+    dt = time.perf_counter() - t
+    srv.close()
+    pts = sum(b.n_z * b.n_screens for b in batch)
+    out["large_runs"]["uneven_batch_64"] = {
+        "screens": int(sum(b.n_screens for b in batch)), "ok": int(sum(x == 0 for x in sts)),
+        "seconds": dt, "screen_points_per_s": pts / dt}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.large:
+        return run_large() if rank == 0 else 0
     return run_ours(args, world, rank, local)
 
 
