@@ -143,6 +143,17 @@ struct swkb_plan {
   std::vector<Graph> graphs;
   bool use_graphs = true;
   bool fuse_reduce = true;   // DFT pass 1 forms the field from the partials
+  // rays on a second stream: a second set of ray and bracket buffers, the
+  // stream, and per set an event "rays ready" and "set free again"
+  bool overlap = false;
+  cudaStream_t ray_stream = nullptr;
+  cudaEvent_t ev_rays[2] = {nullptr, nullptr};
+  cudaEvent_t ev_free[2] = {nullptr, nullptr};
+  void* rd1 = nullptr;
+  void* rph1 = nullptr;
+  void* ra1 = nullptr;
+  int* jlo1 = nullptr;
+  int* jlo_neg1 = nullptr;
 };
 
 namespace {
@@ -433,6 +444,17 @@ swkb_status build_device(swkb_plan* p, const swkb_profile* prof) {
     TRY(dev_alloc(p, (void**)&p->jlo_neg, jn * sizeof(int)));
     CK(cudaMemsetAsync(p->jlo_neg, 0, jn * sizeof(int), p->stream));
   }
+  if (p->overlap) {
+    TRY(dev_alloc(p, &p->rd1, rays * sizeof(T)));
+    TRY(dev_alloc(p, &p->rph1, rays * sizeof(T)));
+    TRY(dev_alloc(p, &p->ra1, rays * sizeof(T)));
+    TRY(dev_alloc(p, (void**)&p->jlo1, jn * sizeof(int)));
+    CK(cudaMemsetAsync(p->jlo1, 0, jn * sizeof(int), p->stream));
+    if (p->sym) {
+      TRY(dev_alloc(p, (void**)&p->jlo_neg1, jn * sizeof(int)));
+      CK(cudaMemsetAsync(p->jlo_neg1, 0, jn * sizeof(int), p->stream));
+    }
+  }
   TRY(dev_alloc(p, (void**)&p->status, sizeof(unsigned)));
   CK(cudaMemsetAsync(p->status, 0, sizeof(unsigned), p->stream));
   TRY(dev_alloc(p, (void**)&p->io, 2 * (size_t)std::max(N, p->n_z) * sizeof(double)));
@@ -453,7 +475,7 @@ swkb_status event_at(swkb_plan* p, int idx) {
 }
 
 template <typename F>
-swkb_status timed(swkb_plan* p, int kind, int n_launches, F&& launch) {
+swkb_status timed_on(swkb_plan* p, cudaStream_t stream, int kind, int n_launches, F&& launch) {
   int e0 = -1, e1 = -1;
   const bool on = ((p->timing >> kind) & 1u) && (p->timing_seen[kind]++ % p->timing_every == 0);
   if (on) {
@@ -462,17 +484,22 @@ swkb_status timed(swkb_plan* p, int kind, int n_launches, F&& launch) {
     TRY(event_at(p, e1));
     // "external" records become event-record nodes when the stream is being
     // captured into a graph (and are plain records otherwise)
-    CK(cudaEventRecordWithFlags(p->events[e0], p->stream, cudaEventRecordExternal));
+    CK(cudaEventRecordWithFlags(p->events[e0], stream, cudaEventRecordExternal));
   }
   CK(launch());
   if (on) {
-    CK(cudaEventRecordWithFlags(p->events[e1], p->stream, cudaEventRecordExternal));
+    CK(cudaEventRecordWithFlags(p->events[e1], stream, cudaEventRecordExternal));
     p->marks.push_back({kind, e0, e1});
     p->stats.kernel_timed[kind] += n_launches;
   }
   p->stats.launches += n_launches;
   p->stats.kernel_launches[kind] += n_launches;
   return SWKB_OK;
+}
+
+template <typename F>
+swkb_status timed(swkb_plan* p, int kind, int n_launches, F&& launch) {
+  return timed_on(p, p->stream, kind, n_launches, launch);
 }
 
 // after the stream has been synchronised
@@ -541,18 +568,20 @@ MarchArgs<T> march_args(const swkb_plan* p, int q) {
 }
 
 template <typename T>
-BracketArgs<T> bracket_args(const swkb_plan* p, const T* d) {
+BracketArgs<T> bracket_args(const swkb_plan* p, const T* d, int* jlo = nullptr,
+                            int* jlo_neg = nullptr) {
   return BracketArgs<T>{d, p->Mr, p->NRT, p->G, p->R, p->N, p->TM, p->n_tiles,
-                        p->jlo, p->sym, p->jlo_neg, p->status};
+                        jlo ? jlo : p->jlo, p->sym, jlo ? jlo_neg : p->jlo_neg, p->status};
 }
 
 template <typename T>
 ResumArgs<T> resum_args(const swkb_plan* p, const T* d, const T* ph, const T* a,
-                        const typename C2<T>::type* c) {
+                        const typename C2<T>::type* c, const int* jlo = nullptr,
+                        const int* jlo_neg = nullptr) {
   using V = typename C2<T>::type;
   ResumArgs<T> ra;
-  ra.d = d; ra.ph = ph; ra.a = a; ra.jlo = p->jlo;
-  ra.jlo_neg = p->jlo_neg;
+  ra.d = d; ra.ph = ph; ra.a = a; ra.jlo = jlo ? jlo : p->jlo;
+  ra.jlo_neg = jlo ? jlo_neg : p->jlo_neg;
   ra.c = c;
   ra.M = p->M; ra.Mr = p->Mr; ra.sym = p->sym; ra.n_tiles_run = p->n_tiles_run; ra.NRT = p->NRT;
   ra.G = p->G; ra.R = p->R; ra.N = p->N; ra.TM = p->TM;
@@ -650,6 +679,92 @@ swkb_status enqueue(swkb_plan* p, const double* u0, int q0, int n, double* out_d
   };
   for (int q = q0; q < q0 + n; ++q) {
     TRY(launch_screen<T>(p, q, fresh));
+    fresh = false;
+    if (snap > 0 && (q - q0 + 1) % snap == 0) {
+      TRY(reduce_to_u<T>(p, true));
+      fresh = true;
+      TRY(emit(k++));
+    }
+  }
+  if (snap <= 0) {
+    if (!fresh) TRY(reduce_to_u<T>(p, true));
+    TRY(emit(0));
+  }
+  return SWKB_OK;
+}
+
+// enqueue() with the rays on a second stream.  A screen's rays depend only on
+// the medium and the mode angles, never on the field, so the march and
+// bracket of screen q (into ray-buffer set (q - q0) % 2, on ray_stream) run
+// beside the DFT of screen q and the resummation of screen q - 1 on the plan
+// stream.  The resummation of screen q waits for its set's "rays" event; the
+// march of screen q + 2 waits for the "free" event recorded after the
+// resummation of screen q, the last reader of that set.  Same kernels and
+// arguments as enqueue(): the fields are bit-identical.
+template <typename T>
+swkb_status enqueue_overlapped(swkb_plan* p, const double* u0, int q0, int n, double* out_dev,
+                               double* out_host, int snap) {
+  using V = typename C2<T>::type;
+  cudaStream_t s = p->stream, sr = p->ray_stream;
+  const int off = p->mirror ? p->n_z : 0;
+  const size_t nb = 2 * sizeof(double) * p->n_z;
+  TRY(timed(p, SWKB_KERNEL_INIT, 1,
+            [&] { return launch_init<T>(u0, p->n_z, p->N, p->mirror, (V*)p->u, s); }));
+  // both sets start free (this also forks ray_stream from the plan stream)
+  CK(cudaEventRecord(p->ev_free[0], s));
+  CK(cudaEventRecord(p->ev_free[1], s));
+  T* rd[2] = {(T*)p->rd, (T*)p->rd1};
+  T* rph[2] = {(T*)p->rph, (T*)p->rph1};
+  T* ra[2] = {(T*)p->ra, (T*)p->ra1};
+  int* jlo[2] = {p->jlo, p->jlo1};
+  int* jneg[2] = {p->jlo_neg, p->jlo_neg1};
+  const bool multi = p->n_cols > 1;
+  bool fresh = true;
+  int k = 0;
+  auto emit = [&](int idx) -> swkb_status {
+    double* dst = out_dev ? out_dev + 2 * (size_t)idx * p->n_z : p->io;
+    TRY(timed(p, SWKB_KERNEL_OUTPUT, 1,
+              [&] { return launch_output<T>((const V*)p->u, off, p->n_z, dst, s); }));
+    if (!out_dev)
+      CK(cudaMemcpyAsync(out_host + 2 * (size_t)idx * p->n_z, p->io, nb, cudaMemcpyDeviceToHost,
+                         s));
+    return SWKB_OK;
+  };
+  for (int q = q0; q < q0 + n; ++q) {
+    const int b = (q - q0) & 1;
+    // rays of screen q
+    CK(cudaStreamWaitEvent(sr, p->ev_free[b], 0));
+    MarchArgs<T> ma = march_args<T>(p, q);
+    ma.out_d = rd[b]; ma.out_ph = rph[b]; ma.out_a = ra[b];
+    TRY(timed_on(p, sr, SWKB_KERNEL_MARCH, 1, [&] { return launch_march<T>(ma, multi, sr); }));
+    const BracketArgs<T> br = bracket_args<T>(p, rd[b], jlo[b], jneg[b]);
+    TRY(timed_on(p, sr, SWKB_KERNEL_BRACKET, 1, [&] { return launch_bracket<T>(br, sr); }));
+    CK(cudaEventRecord(p->ev_rays[b], sr));
+    // modes of screen q (pass 1 forms the field from the partials itself)
+    const bool fuse = p->fuse_reduce && !fresh && p->N1 > 1 && (p->sym || !p->mirror);
+    if (!fresh && !fuse) {
+      ReduceArgs<T> r{(const V*)p->part, p->n_groups, p->N, (const T*)p->W, p->mirror, p->sym,
+                      (V*)p->u};
+      TRY(timed(p, SWKB_KERNEL_REDUCE, 1, [&] { return launch_reduce<T>(r, s); }));
+    }
+    FftArgs<T> f;
+    f.u = (const V*)p->u; f.tw = (const V*)p->tw; f.Y = (V*)p->Y;
+    f.N = p->N; f.N1 = p->N1; f.N2 = p->N2; f.log2N2 = p->log2N2; f.n_max = p->n_max;
+    f.mirror = p->mirror;
+    f.part = fuse ? (const V*)p->part : nullptr;
+    f.n_part = p->n_groups;
+    f.sym = p->sym;
+    f.W = (const T*)p->W;
+    f.inv_N = (T)(1.0 / p->N);
+    f.ephi = (const V*)p->ephi_d; f.c = (V*)p->c;
+    TRY(timed(p, SWKB_KERNEL_FFT, p->N1 > 1 ? 2 : 1, [&] { return launch_fft<T>(f, s); }));
+    // the sum of screen q, once its rays are there
+    CK(cudaStreamWaitEvent(s, p->ev_rays[b], 0));
+    const ResumArgs<T> rs = resum_args<T>(p, rd[b], rph[b], ra[b], (const V*)p->c, jlo[b],
+                                          jneg[b]);
+    TRY(timed(p, SWKB_KERNEL_RESUM, 1, [&] { return launch_resum<T>(rs, s); }));
+    CK(cudaEventRecord(p->ev_free[b], s));
+    p->stats.screens += 1;
     fresh = false;
     if (snap > 0 && (q - q0 + 1) % snap == 0) {
       TRY(reduce_to_u<T>(p, true));
@@ -782,7 +897,8 @@ swkb_status run_graph(swkb_plan* p, const double* u0, int q0, int n, double* dst
     const swkb_plan_stats before = p->stats;
     p->marks.clear();
     CK(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
-    swkb_status st = enqueue<T>(p, u0, q0, n, dst, nullptr, snap);
+    swkb_status st = p->overlap ? enqueue_overlapped<T>(p, u0, q0, n, dst, nullptr, snap)
+                                : enqueue<T>(p, u0, q0, n, dst, nullptr, snap);
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(p->stream, &graph);
     if (st == SWKB_OK && ec != cudaSuccess)
@@ -834,7 +950,8 @@ swkb_status run(swkb_plan* p, const double* u0, int q0, int n, double* out_dev, 
                          p->stream));
     return read_status(p);
   }
-  TRY(enqueue<T>(p, u0, q0, n, out_dev, out_host, snap));
+  TRY(p->overlap ? enqueue_overlapped<T>(p, u0, q0, n, out_dev, out_host, snap)
+                 : enqueue<T>(p, u0, q0, n, out_dev, out_host, snap));
   return read_status(p);
 }
 
@@ -906,6 +1023,11 @@ void release(swkb_plan* p) {
   drop_graphs(p);
   for (void* ptr : p->allocs) cudaFree(ptr);
   for (cudaEvent_t e : p->events) cudaEventDestroy(e);
+  for (int b = 0; b < 2; ++b) {
+    if (p->ev_rays[b]) cudaEventDestroy(p->ev_rays[b]);
+    if (p->ev_free[b]) cudaEventDestroy(p->ev_free[b]);
+  }
+  if (p->ray_stream) cudaStreamDestroy(p->ray_stream);
   if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
   cudaSetDevice(cur);
   delete p;
@@ -1116,6 +1238,12 @@ swkb_status configure(swkb_plan* p, const swkb_profile* prof, double k, const sw
   CK(cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device));
   p->autotune = opt.autotune != 0;
   p->reuse_rays = opt.reuse_rays != 0 && p->n_cols == 1;
+  // rays on a second stream unless they are reused (SWKB_OVERLAP=0: one
+  // stream, one ray-buffer set)
+  {
+    const char* oe = getenv("SWKB_OVERLAP");
+    p->overlap = !(oe && oe[0] == '0') && !p->reuse_rays;
+  }
   p->planes = opt.planes > 1 ? opt.planes : 0;
   if (p->planes && (p->planes > p->Nt || p->Nt % p->planes))
     return fail(SWKB_ERR_INVALID_ARG, "planes (%d) must divide rk4_steps (%d)", p->planes, p->Nt);
@@ -1146,11 +1274,12 @@ size_t device_bytes(const swkb_plan* p) {
   b += (size_t)p->N * V;                                            // twiddles
   if (p->absorber_frac > 0) b += (size_t)p->N * T;                  // absorber
   b += (size_t)p->N * V * (2 + (size_t)p->alloc_groups) + (size_t)p->M * V;  // u, Y, partials, c
-  b += 3 * (size_t)p->NRT * p->Mr * T;                              // rays
+  b += 3 * (size_t)p->NRT * p->Mr * T * (p->overlap ? 2 : 1);     // rays (one or two sets)
   if (p->planes > 1)                                                 // inner planes
     b += (size_t)(p->planes - 1) * (3 * (size_t)p->NRT * p->Mr * T + (size_t)p->M * V) +
          (size_t)p->M * V;
-  b += (size_t)(p->alloc_tiles + 1) * p->Mr * sizeof(int) * (p->sym ? 2 : 1);
+  b += (size_t)(p->alloc_tiles + 1) * p->Mr * sizeof(int) * (p->sym ? 2 : 1) *
+       (p->overlap ? 2 : 1);
   b += 16 + 2 * (size_t)std::max(p->N, p->n_z) * sizeof(double);   // status, io
   return b;
 }
@@ -1330,6 +1459,13 @@ swkb_status swkb_plan_create(const swkb_profile* prof, double k, const swkb_doma
     } else {
       CK(cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking));
       p->own_stream = true;
+    }
+    if (p->overlap) {
+      CK(cudaStreamCreateWithFlags(&p->ray_stream, cudaStreamNonBlocking));
+      for (int b = 0; b < 2; ++b) {
+        CK(cudaEventCreateWithFlags(&p->ev_rays[b], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&p->ev_free[b], cudaEventDisableTiming));
+      }
     }
     swkb_status st = p->precision == SWKB_FP64 ? build_device<double>(p, prof)
                                                : build_device<float>(p, prof);
