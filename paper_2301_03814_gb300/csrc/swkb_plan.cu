@@ -1339,6 +1339,7 @@ swkb_status autotune_plan(swkb_plan* p) {
   CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   CK(cudaMemsetAsync(p->u, 0, (size_t)p->N * sizeof(V), p->stream));
   CK(cudaMemsetAsync(p->part, 0, (size_t)p->alloc_groups * p->N * sizeof(V), p->stream));
+  CK(cudaMemsetAsync(p->io, 0, 2 * (size_t)std::max(p->N, p->n_z) * sizeof(double), p->stream));
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
@@ -1349,12 +1350,23 @@ swkb_status autotune_plan(swkb_plan* p) {
     apply_tiling(p, t);
     p->rays_ready = false;   // brackets depend on the tile size
     if (resum_smem_bytes<T>(p->wcap, p->TM) > (size_t)optin) continue;
-    st = launch_screen<T>(p, 0, true);
+    // time what a propagation runs: with rays on their own stream, four
+    // overlapped screens (zero field in and out of the staging buffer);
+    // otherwise two screens after a warm-up screen
+    if (p->overlap) {
+      st = enqueue_overlapped<T>(p, p->io, 0, 1, p->io, nullptr, 0);
+    } else {
+      st = launch_screen<T>(p, 0, true);
+    }
     if (st != SWKB_OK) break;
     float ms = 1e30f;
     for (int trial = 0; trial < 3 && st == SWKB_OK; ++trial) {   // min of 3 trials
       cudaEventRecord(e0, p->stream);
-      for (int r = 1; r <= 2 && st == SWKB_OK; ++r) st = launch_screen<T>(p, r, false);
+      if (p->overlap) {
+        st = enqueue_overlapped<T>(p, p->io, 0, 4, p->io, nullptr, 0);
+      } else {
+        for (int r = 1; r <= 2 && st == SWKB_OK; ++r) st = launch_screen<T>(p, r, false);
+      }
       if (st != SWKB_OK) break;
       cudaEventRecord(e1, p->stream);
       cudaError_t e = cudaEventSynchronize(e1);
