@@ -277,13 +277,14 @@ int choose_pieces(const swkb_plan* p, const std::vector<double>& coef) {
       E2 = std::max(E2, fabs(d2) / (h * h));
     }
   }
-  const long long ext = (long long)(p->mirror ? 2 : 1) * p->n_int;
-  for (int S = 1; S <= 16; S *= 2) {
-    if (ext * S >= (1LL << 22)) break;            // FP32 positions stay exact below 2^22
-    bool ok = true;
-    for (size_t i = 0; i < n && ok; ++i) {
+  const double tol[3] = {1e-7 * E0, 1e-6 * E1, 1e-4 * E2};
+  // largest deviations of S pieces from the quintic (value, slope, curvature);
+  // with stop set, returns as soon as one exceeds its bound
+  auto worst = [&](int S, double dev[3], bool stop) {
+    dev[0] = dev[1] = dev[2] = 0.0;
+    for (size_t i = 0; i < n; ++i) {
       const double* a = coef.data() + i * 8;
-      for (int s = 0; s < S && ok; ++s) {
+      for (int s = 0; s < S; ++s) {
         double b[4];
         cubic_piece(a, s, S, b);
         for (double tau : {0.25, 0.5, 0.75}) {
@@ -292,17 +293,67 @@ int choose_pieces(const swkb_plan* p, const std::vector<double>& coef) {
           const double cv = ((b[3] * tau + b[2]) * tau + b[1]) * tau + b[0];
           const double c1 = ((3.0 * b[3] * tau + 2.0 * b[2]) * tau + b[1]) * S;
           const double c2 = (6.0 * b[3] * tau + 2.0 * b[2]) * S * S;
-          if (fabs(cv - v) > 1e-7 * E0 || fabs(c1 - d1) / h > 1e-6 * E1 ||
-              fabs(c2 - d2) / (h * h) > 1e-4 * E2) {
-            ok = false;
-            break;
-          }
+          dev[0] = std::max(dev[0], fabs(cv - v));
+          dev[1] = std::max(dev[1], fabs(c1 - d1) / h);
+          dev[2] = std::max(dev[2], fabs(c2 - d2) / (h * h));
+          if (stop && (dev[0] > tol[0] || dev[1] > tol[1] || dev[2] > tol[2])) return false;
         }
       }
     }
-    if (ok) return S;
+    return dev[0] <= tol[0] && dev[1] <= tol[1] && dev[2] <= tol[2];
+  };
+  double dev[3];
+  if (worst(1, dev, false)) return 1;
+  // cubic Hermite errors fall as S^-4 (value), S^-3 (slope), S^-2 (curvature):
+  // start from the S the single-piece deviations predict, then verify
+  auto ratio = [](double d, double t) { return t > 0 ? d / t : (d > 0 ? 1e300 : 0.0); };
+  const double need = std::max({pow(ratio(dev[0], tol[0]), 0.25), pow(ratio(dev[1], tol[1]), 1.0 / 3.0),
+                                sqrt(ratio(dev[2], tol[2]))});
+  const long long ext = (long long)(p->mirror ? 2 : 1) * p->n_int;
+  int S = 2;
+  while (S < need && S < 16) S *= 2;
+  for (; S <= 16; S *= 2) {
+    if (ext * S >= (1LL << 22)) break;            // FP32 positions stay exact below 2^22
+    if (worst(S, dev, true)) return S;
   }
   return 0;
+}
+
+// choose_pieces depends only on the table (and eps_ref, the ground
+// reflection): remembered by a 64-bit FNV-1a hash of those, so that the
+// budget estimate and the creation of the same request's plan scan it once.
+uint64_t table_hash(const swkb_plan* p, const swkb_profile* prof) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](const void* data, size_t bytes) {
+    const unsigned char* c = (const unsigned char*)data;
+    for (size_t i = 0; i < bytes; ++i) { h ^= c[i]; h *= 1099511628211ull; }
+  };
+  const size_t nt = (size_t)p->n_cols * p->n_p;
+  mix(prof->eps, nt * sizeof(double));
+  mix(prof->eps_z, nt * sizeof(double));
+  mix(prof->eps_zz, nt * sizeof(double));
+  const double sc[2] = {p->eps_ref, p->dzp};
+  const int ic[3] = {p->n_cols, p->n_p, p->mirror};
+  mix(sc, sizeof(sc));
+  mix(ic, sizeof(ic));
+  return h;
+}
+
+std::mutex g_pieces_mutex;
+std::map<uint64_t, int> g_pieces_cache;
+
+int pieces_for(const swkb_plan* p, const swkb_profile* prof) {
+  const uint64_t key = table_hash(p, prof);
+  {
+    std::lock_guard<std::mutex> lk(g_pieces_mutex);
+    auto it = g_pieces_cache.find(key);
+    if (it != g_pieces_cache.end()) return it->second;
+  }
+  const int S = choose_pieces(p, quintic_coefficients(p, prof));
+  std::lock_guard<std::mutex> lk(g_pieces_mutex);
+  if (g_pieces_cache.size() >= 256) g_pieces_cache.clear();
+  g_pieces_cache[key] = S;
+  return S;
 }
 
 template <typename T>
@@ -693,6 +744,55 @@ swkb_status enqueue(swkb_plan* p, const double* u0, int q0, int n, double* out_d
   return SWKB_OK;
 }
 
+// One screen of the overlapped sequence: rays of screen q into ray-buffer set
+// b on ray_stream, modes of the field on the plan stream, then the sum once
+// the rays are there.  ev_free[b] must have been recorded (set free).
+template <typename T>
+swkb_status overlapped_screen(swkb_plan* p, int q, int b, bool fresh) {
+  using V = typename C2<T>::type;
+  cudaStream_t s = p->stream, sr = p->ray_stream;
+  T* rd[2] = {(T*)p->rd, (T*)p->rd1};
+  T* rph[2] = {(T*)p->rph, (T*)p->rph1};
+  T* ra[2] = {(T*)p->ra, (T*)p->ra1};
+  int* jlo[2] = {p->jlo, p->jlo1};
+  int* jneg[2] = {p->jlo_neg, p->jlo_neg1};
+  const bool multi = p->n_cols > 1;
+  // rays of screen q
+  CK(cudaStreamWaitEvent(sr, p->ev_free[b], 0));
+  MarchArgs<T> ma = march_args<T>(p, q);
+  ma.out_d = rd[b]; ma.out_ph = rph[b]; ma.out_a = ra[b];
+  TRY(timed_on(p, sr, SWKB_KERNEL_MARCH, 1, [&] { return launch_march<T>(ma, multi, sr); }));
+  const BracketArgs<T> br = bracket_args<T>(p, rd[b], jlo[b], jneg[b]);
+  TRY(timed_on(p, sr, SWKB_KERNEL_BRACKET, 1, [&] { return launch_bracket<T>(br, sr); }));
+  CK(cudaEventRecord(p->ev_rays[b], sr));
+  // modes of screen q (pass 1 forms the field from the partials itself)
+  const bool fuse = p->fuse_reduce && !fresh && p->N1 > 1 && (p->sym || !p->mirror);
+  if (!fresh && !fuse) {
+    ReduceArgs<T> r{(const V*)p->part, p->n_groups, p->N, (const T*)p->W, p->mirror, p->sym,
+                    (V*)p->u};
+    TRY(timed(p, SWKB_KERNEL_REDUCE, 1, [&] { return launch_reduce<T>(r, s); }));
+  }
+  FftArgs<T> f;
+  f.u = (const V*)p->u; f.tw = (const V*)p->tw; f.Y = (V*)p->Y;
+  f.N = p->N; f.N1 = p->N1; f.N2 = p->N2; f.log2N2 = p->log2N2; f.n_max = p->n_max;
+  f.mirror = p->mirror;
+  f.part = fuse ? (const V*)p->part : nullptr;
+  f.n_part = p->n_groups;
+  f.sym = p->sym;
+  f.W = (const T*)p->W;
+  f.inv_N = (T)(1.0 / p->N);
+  f.ephi = (const V*)p->ephi_d; f.c = (V*)p->c;
+  TRY(timed(p, SWKB_KERNEL_FFT, p->N1 > 1 ? 2 : 1, [&] { return launch_fft<T>(f, s); }));
+  // the sum of screen q, once its rays are there
+  CK(cudaStreamWaitEvent(s, p->ev_rays[b], 0));
+  const ResumArgs<T> rs = resum_args<T>(p, rd[b], rph[b], ra[b], (const V*)p->c, jlo[b],
+                                        jneg[b]);
+  TRY(timed(p, SWKB_KERNEL_RESUM, 1, [&] { return launch_resum<T>(rs, s); }));
+  CK(cudaEventRecord(p->ev_free[b], s));
+  p->stats.screens += 1;
+  return SWKB_OK;
+}
+
 // enqueue() with the rays on a second stream.  A screen's rays depend only on
 // the medium and the mode angles, never on the field, so the march and
 // bracket of screen q (into ray-buffer set (q - q0) % 2, on ray_stream) run
@@ -705,7 +805,7 @@ template <typename T>
 swkb_status enqueue_overlapped(swkb_plan* p, const double* u0, int q0, int n, double* out_dev,
                                double* out_host, int snap) {
   using V = typename C2<T>::type;
-  cudaStream_t s = p->stream, sr = p->ray_stream;
+  cudaStream_t s = p->stream;
   const int off = p->mirror ? p->n_z : 0;
   const size_t nb = 2 * sizeof(double) * p->n_z;
   TRY(timed(p, SWKB_KERNEL_INIT, 1,
@@ -713,12 +813,6 @@ swkb_status enqueue_overlapped(swkb_plan* p, const double* u0, int q0, int n, do
   // both sets start free (this also forks ray_stream from the plan stream)
   CK(cudaEventRecord(p->ev_free[0], s));
   CK(cudaEventRecord(p->ev_free[1], s));
-  T* rd[2] = {(T*)p->rd, (T*)p->rd1};
-  T* rph[2] = {(T*)p->rph, (T*)p->rph1};
-  T* ra[2] = {(T*)p->ra, (T*)p->ra1};
-  int* jlo[2] = {p->jlo, p->jlo1};
-  int* jneg[2] = {p->jlo_neg, p->jlo_neg1};
-  const bool multi = p->n_cols > 1;
   bool fresh = true;
   int k = 0;
   auto emit = [&](int idx) -> swkb_status {
@@ -731,40 +825,7 @@ swkb_status enqueue_overlapped(swkb_plan* p, const double* u0, int q0, int n, do
     return SWKB_OK;
   };
   for (int q = q0; q < q0 + n; ++q) {
-    const int b = (q - q0) & 1;
-    // rays of screen q
-    CK(cudaStreamWaitEvent(sr, p->ev_free[b], 0));
-    MarchArgs<T> ma = march_args<T>(p, q);
-    ma.out_d = rd[b]; ma.out_ph = rph[b]; ma.out_a = ra[b];
-    TRY(timed_on(p, sr, SWKB_KERNEL_MARCH, 1, [&] { return launch_march<T>(ma, multi, sr); }));
-    const BracketArgs<T> br = bracket_args<T>(p, rd[b], jlo[b], jneg[b]);
-    TRY(timed_on(p, sr, SWKB_KERNEL_BRACKET, 1, [&] { return launch_bracket<T>(br, sr); }));
-    CK(cudaEventRecord(p->ev_rays[b], sr));
-    // modes of screen q (pass 1 forms the field from the partials itself)
-    const bool fuse = p->fuse_reduce && !fresh && p->N1 > 1 && (p->sym || !p->mirror);
-    if (!fresh && !fuse) {
-      ReduceArgs<T> r{(const V*)p->part, p->n_groups, p->N, (const T*)p->W, p->mirror, p->sym,
-                      (V*)p->u};
-      TRY(timed(p, SWKB_KERNEL_REDUCE, 1, [&] { return launch_reduce<T>(r, s); }));
-    }
-    FftArgs<T> f;
-    f.u = (const V*)p->u; f.tw = (const V*)p->tw; f.Y = (V*)p->Y;
-    f.N = p->N; f.N1 = p->N1; f.N2 = p->N2; f.log2N2 = p->log2N2; f.n_max = p->n_max;
-    f.mirror = p->mirror;
-    f.part = fuse ? (const V*)p->part : nullptr;
-    f.n_part = p->n_groups;
-    f.sym = p->sym;
-    f.W = (const T*)p->W;
-    f.inv_N = (T)(1.0 / p->N);
-    f.ephi = (const V*)p->ephi_d; f.c = (V*)p->c;
-    TRY(timed(p, SWKB_KERNEL_FFT, p->N1 > 1 ? 2 : 1, [&] { return launch_fft<T>(f, s); }));
-    // the sum of screen q, once its rays are there
-    CK(cudaStreamWaitEvent(s, p->ev_rays[b], 0));
-    const ResumArgs<T> rs = resum_args<T>(p, rd[b], rph[b], ra[b], (const V*)p->c, jlo[b],
-                                          jneg[b]);
-    TRY(timed(p, SWKB_KERNEL_RESUM, 1, [&] { return launch_resum<T>(rs, s); }));
-    CK(cudaEventRecord(p->ev_free[b], s));
-    p->stats.screens += 1;
+    TRY(overlapped_screen<T>(p, q, (q - q0) & 1, fresh));
     fresh = false;
     if (snap > 0 && (q - q0 + 1) % snap == 0) {
       TRY(reduce_to_u<T>(p, true));
@@ -1224,7 +1285,7 @@ swkb_status configure(swkb_plan* p, const swkb_profile* prof, double k, const sw
     if (!(p->eps_ref - kmax * kmax > 0))
       return fail(SWKB_ERR_INVALID_ARG, "steepest kept mode is evanescent at eps_ref");
   }
-  p->pieces = p->precision == SWKB_FP64 ? 0 : choose_pieces(p, quintic_coefficients(p, prof));
+  p->pieces = p->precision == SWKB_FP64 ? 0 : pieces_for(p, prof);
   if (p->n_cols > 1) {
     const double q_end = ceil((p->x_cols.back() - p->x0) / p->dx);
     p->stage_rows = (int)std::min(std::max(q_end, 0.0), 1e6) + 1;
@@ -1296,6 +1357,10 @@ swkb_status begin_t(swkb_plan* p, const double* u0_host) {
                      p->stream));
   TRY(timed(p, SWKB_KERNEL_INIT, 1,
             [&] { return launch_init<T>(p->io, p->n_z, p->N, p->mirror, (V*)p->u, p->stream); }));
+  if (p->overlap) {   // both ray-buffer sets free
+    CK(cudaEventRecord(p->ev_free[0], p->stream));
+    CK(cudaEventRecord(p->ev_free[1], p->stream));
+  }
   return SWKB_OK;
 }
 
@@ -1410,10 +1475,18 @@ swkb_status plan_begin(swkb_plan* p, const double* u0_host) {
 
 swkb_status plan_advance(swkb_plan* p, int q, int n, bool first) {
   CK(cudaSetDevice(p->device));
+  // with rays on their own stream, screens alternate between the two ray-buffer
+  // sets by the parity of their index
   for (int i = 0; i < n; ++i) {
     const bool fresh = first && i == 0;
-    swkb_status st = p->precision == SWKB_FP64 ? launch_screen<double>(p, q + i, fresh)
-                                               : launch_screen<float>(p, q + i, fresh);
+    const int qi = q + i;
+    swkb_status st;
+    if (p->overlap)
+      st = p->precision == SWKB_FP64 ? overlapped_screen<double>(p, qi, qi & 1, fresh)
+                                     : overlapped_screen<float>(p, qi, qi & 1, fresh);
+    else
+      st = p->precision == SWKB_FP64 ? launch_screen<double>(p, qi, fresh)
+                                     : launch_screen<float>(p, qi, fresh);
     if (st != SWKB_OK) return st;
   }
   return SWKB_OK;
