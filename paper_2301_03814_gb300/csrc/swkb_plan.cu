@@ -745,8 +745,8 @@ swkb_status enqueue(swkb_plan* p, const double* u0, int q0, int n, double* out_d
 }
 
 // One screen of the overlapped sequence: rays of screen q into ray-buffer set
-// b on ray_stream, modes of the field on the plan stream, then the sum once
-// the rays are there.  ev_free[b] must have been recorded (set free).
+// b on ray_stream, modes of the field on the plan stream, then brackets and
+// sum once the rays are there.  ev_free[b] must have been recorded (set free).
 template <typename T>
 swkb_status overlapped_screen(swkb_plan* p, int q, int b, bool fresh) {
   using V = typename C2<T>::type;
@@ -762,8 +762,6 @@ swkb_status overlapped_screen(swkb_plan* p, int q, int b, bool fresh) {
   MarchArgs<T> ma = march_args<T>(p, q);
   ma.out_d = rd[b]; ma.out_ph = rph[b]; ma.out_a = ra[b];
   TRY(timed_on(p, sr, SWKB_KERNEL_MARCH, 1, [&] { return launch_march<T>(ma, multi, sr); }));
-  const BracketArgs<T> br = bracket_args<T>(p, rd[b], jlo[b], jneg[b]);
-  TRY(timed_on(p, sr, SWKB_KERNEL_BRACKET, 1, [&] { return launch_bracket<T>(br, sr); }));
   CK(cudaEventRecord(p->ev_rays[b], sr));
   // modes of screen q (pass 1 forms the field from the partials itself)
   const bool fuse = p->fuse_reduce && !fresh && p->N1 > 1 && (p->sym || !p->mirror);
@@ -783,8 +781,11 @@ swkb_status overlapped_screen(swkb_plan* p, int q, int b, bool fresh) {
   f.inv_N = (T)(1.0 / p->N);
   f.ephi = (const V*)p->ephi_d; f.c = (V*)p->c;
   TRY(timed(p, SWKB_KERNEL_FFT, p->N1 > 1 ? 2 : 1, [&] { return launch_fft<T>(f, s); }));
-  // the sum of screen q, once its rays are there
+  // brackets and sum of screen q, once its rays are there (the ray stream
+  // goes on with the next march)
   CK(cudaStreamWaitEvent(s, p->ev_rays[b], 0));
+  const BracketArgs<T> br = bracket_args<T>(p, rd[b], jlo[b], jneg[b]);
+  TRY(timed(p, SWKB_KERNEL_BRACKET, 1, [&] { return launch_bracket<T>(br, s); }));
   const ResumArgs<T> rs = resum_args<T>(p, rd[b], rph[b], ra[b], (const V*)p->c, jlo[b],
                                         jneg[b]);
   TRY(timed(p, SWKB_KERNEL_RESUM, 1, [&] { return launch_resum<T>(rs, s); }));
@@ -794,12 +795,12 @@ swkb_status overlapped_screen(swkb_plan* p, int q, int b, bool fresh) {
 }
 
 // enqueue() with the rays on a second stream.  A screen's rays depend only on
-// the medium and the mode angles, never on the field, so the march and
-// bracket of screen q (into ray-buffer set (q - q0) % 2, on ray_stream) run
-// beside the DFT of screen q and the resummation of screen q - 1 on the plan
-// stream.  The resummation of screen q waits for its set's "rays" event; the
-// march of screen q + 2 waits for the "free" event recorded after the
-// resummation of screen q, the last reader of that set.  Same kernels and
+// the medium and the mode angles, never on the field, so the march of screen
+// q (into ray-buffer set (q - q0) % 2, on ray_stream) runs beside the DFT of
+// screen q and the bracket and resummation of screen q - 1 on the plan stream.
+// The bracket of screen q waits for its set's "rays" event; the march of
+// screen q + 2 waits for the "free" event recorded after the resummation of
+// screen q, the last reader of that set.  Same kernels and
 // arguments as enqueue(): the fields are bit-identical.
 template <typename T>
 swkb_status enqueue_overlapped(swkb_plan* p, const double* u0, int q0, int n, double* out_dev,
