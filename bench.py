@@ -450,6 +450,18 @@ def run_ours(args, world, rank, local):
     e2e = {"value": points_per_step * world / t_e2e, "unit": UNIT,
            "h2d_bytes_per_step": int(h_in.numel() * 16), "d2h_bytes_per_step": int(h_out.numel() * 16)}
 
+    # FP64 march against the FP64 peak (2 DFMA per SM per clock, the rate ncu
+    # reports): events around every FP64 launch of the FP64 steps
+    peak_fp64 = 152 * 2 * 2 * 2.07e9 / 1e12
+    fp64_roof = None
+    info64 = plan64.info
+    if st64["kernel_timed"]["march"]:
+        per64 = st64["kernel_ms"]["march"] / 1e3 / st64["kernel_timed"]["march"]
+        ach64 = march_flops_per_ray(pb) * info64.march_modes * info64.n_rays_total / per64 / 1e12
+        fp64_roof = {"bound": "alu", "achieved": ach64, "peak": peak_fp64, "unit": "TFLOP/s",
+                     "frac": ach64 / peak_fp64, "launch_ms": per64 * 1e3,
+                     "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"}
+
     # roofline of the dominant kernel (live event times of the timed region)
     kms = st["kernel_ms"]
     kl = st["kernel_launches"]
@@ -485,7 +497,8 @@ def run_ours(args, world, rank, local):
             "tiling": {"tile_points": info.tile_points, "mode_groups": info.mode_groups,
                        "fft_n1": info.fft_n1, "autotuned": tune},
             "fp64": {"value": value64, "unit": UNIT, "ms_per_step": statistics.mean(ts64),
-                     "steps": len(ts64), "kernel_ms_per_step": {k: v / len(ts64) for k, v in st64["kernel_ms"].items()}},
+                     "steps": len(ts64), "kernel_ms_per_step": {k: v / len(ts64) for k, v in st64["kernel_ms"].items()},
+                     "march_roofline": fp64_roof},
             "mixed_vs_fp64_rel_l2": err,
             "x_invariant_ray_reuse": reuse,
             "kernel_ms_per_step": kms_all,

@@ -305,3 +305,20 @@ def test_fp32_medium_pieces():
     assert swkb.Plan(duct, swkb.SWKB_MIXED).info.medium_pieces == 16
     assert swkb.Plan(duct, swkb.SWKB_FP64).info.medium_pieces == 0
     assert swkb.Plan(w.config_gaussian_medium(), swkb.SWKB_MIXED).info.medium_pieces == 1
+
+
+@pytest.mark.parametrize("prec", [swkb.SWKB_FP64, swkb.SWKB_MIXED])
+def test_rays_on_their_own_stream_give_identical_fields(prec, monkeypatch):
+    # the overlapped sequence (march on a second stream, two ray-buffer sets)
+    # runs the same kernels on the same arguments as the one-stream sequence:
+    # snapshots and a range-dependent medium included, the fields are equal
+    pb = duct_small()
+    pr = pb.profile
+    rd = pb.with_(profile=w._table([0.0, 150.0], pr.z0, pr.dz, pr.n_p,
+                                   [w.f_trilinear_duct(12.0, -0.1), w.f_trilinear_duct(15.0, -0.1)]))
+    for case in (pb, rd):
+        monkeypatch.setenv("SWKB_OVERLAP", "0")
+        one = swkb.Plan(case, prec).propagate(snapshot_every=2)
+        monkeypatch.delenv("SWKB_OVERLAP")
+        two = swkb.Plan(case, prec).propagate(snapshot_every=2)
+        assert np.array_equal(one, two)
