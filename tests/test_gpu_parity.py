@@ -322,3 +322,18 @@ def test_rays_on_their_own_stream_give_identical_fields(prec, monkeypatch):
         monkeypatch.delenv("SWKB_OVERLAP")
         two = swkb.Plan(case, prec).propagate(snapshot_every=2)
         assert np.array_equal(one, two)
+
+
+_batch_cache = {}
+
+
+@pytest.mark.parametrize("idx", [12, 33], ids=["trilinear", "evaporation"])
+@pytest.mark.parametrize("prec,tol", [(swkb.SWKB_FP64, FP64_TOL), (swkb.SWKB_MIXED, MIXED_TOL)])
+def test_uneven_batch_instances_match_oracle(idx, prec, tol):
+    # two of the 64 uneven instances (seeded draw: frequency, height, N_z,
+    # profile kind), the first two screens of each
+    pb = w.batch_uneven(4, 64)[idx].with_(n_screens=2)
+    if idx not in _batch_cache:
+        _batch_cache[idx] = Oracle(pb).propagate(pb.u0)
+    got = swkb.Plan(pb, prec).propagate()
+    assert rel_l2(got, _batch_cache[idx]) < tol
