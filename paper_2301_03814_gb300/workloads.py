@@ -299,6 +299,41 @@ def config_gaussian_medium(a=0.02, b=0.01, n_z=256, height=64.0, dx=10.0, n_scre
                    meta={"tilt_deg": tilt})
 
 
+def config_gaussian_layer(a, b, height, n_z, range_m, n_screens, n_max, lam=0.05, w0=60.0,
+                          tilt_deg=0.0, ray_stride=16, rk4_steps=16):
+    """Periodic domain [-height/2, height/2) around a Gaussian permittivity
+    layer eps = 1 + a exp(-b z^2) (the paper's exponential model, centred),
+    x-invariant; Gaussian beam of waist w0 at z = 0, tilted by tilt_deg;
+    n_max fixes the kept modes."""
+    k = 2.0 * math.pi / lam
+    dx = range_m / n_screens
+    z0 = -height / 2 - 2.0 * dx * 0.05 - 8.0
+    dzp = 0.05
+    n_p = int(math.ceil((height + 2.0 * (-height / 2 - z0)) / dzp)) + 1
+    prof = _table([0.0], z0, dzp, n_p, [f_gaussian(a, b)])
+    z = -height / 2 + height / n_z * np.arange(n_z)
+    u0 = gaussian_beam(z, k, 0.0, w0, math.radians(tilt_deg))
+    return Problem(f"gaussian-layer-{n_z}", k, -height / 2, height / 2, n_z, BC_PERIODIC, 0.0,
+                   dx, n_screens, prof, u0, math.radians(89.0), ray_stride, rk4_steps, 0.0,
+                   n_max=n_max, meta={"a": a, "b": b})
+
+
+def config_gaussian_lens_40km(**kw):
+    """A single-focus lens like the paper's first example: eps = 1 + 1e-4
+    exp(-1e-4 z^2), lambda = 5 cm, 401 modes, 40 km in 40 screens of 1 km,
+    600 m periodic domain, 60 m beam (focus near 16 km)."""
+    return config_gaussian_layer(1e-4, 1e-4, 600.0, 4096, 40_000.0, 40, 200, **kw)
+
+
+def config_gaussian_duct_200km(**kw):
+    """A narrow duct like the paper's second example: eps = 1 + 1e-4
+    exp(-1e-3 z^2), lambda = 5 cm, beam tilted 0.2 deg, 200 km in 200 screens
+    of 1 km (about ten oscillations in the duct), 400 m periodic domain, 241
+    modes."""
+    return config_gaussian_layer(1e-4, 1e-3, 400.0, 4096, 200_000.0, 200, 120, w0=10.0,
+                                 tilt_deg=0.2, **kw)
+
+
 def config_surface_duct(seed=2, height=200.0, n_z=16384, range_m=10_000.0, n_screens=200,
                         lam=0.05, theta_bw_deg=1.0, z_s=10.0, z_t_range=(20.0, 60.0),
                         g_d_range=(-0.2, -0.05), theta_max_deg=3.5, ray_stride=16,
