@@ -1082,6 +1082,9 @@ void release(swkb_plan* p) {
   int cur = 0;
   cudaGetDevice(&cur);
   cudaSetDevice(p->device);
+  // a sequence that failed between a march and the wait that joins it may
+  // leave work on the ray stream: finish it before its buffers go
+  if (p->ray_stream) cudaStreamSynchronize(p->ray_stream);
   drop_graphs(p);
   for (void* ptr : p->allocs) cudaFree(ptr);
   for (cudaEvent_t e : p->events) cudaEventDestroy(e);
