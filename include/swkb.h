@@ -109,7 +109,12 @@ typedef struct {
                              shapes (resummation tile and CTAs per SM, DFT
                              split) on the plan's buffers and keep the
                              fastest; cached per shape for the process       */
-  void* cuda_stream;      /* cudaStream_t to run on; NULL = a library stream  */
+  void* cuda_stream;      /* cudaStream_t to run on; NULL = a library stream.
+                             The plan also owns a second stream for the ray
+                             march (unless SWKB_OVERLAP=0 or reuse_rays):
+                             within every call it forks from this stream and
+                             joins back into it, so results are ordered on
+                             this stream as if one stream ran everything     */
   int32_t device;         /* CUDA device ordinal                              */
   int32_t reuse_rays;     /* 1: for a range-independent medium (one table
                              column) march the rays once per propagate call
