@@ -15,6 +15,7 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -23,12 +24,19 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "swkb.h"
 #include "swkb_internal.h"
 
 using namespace swkb;
 
 namespace {
+// NVTX range for profilers (ncu --nvtx, nsys); a no-op without one attached
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
 
 thread_local std::string g_err;
 
@@ -122,6 +130,7 @@ struct swkb_plan {
   void* stage_th = nullptr;
   double* io = nullptr;  // complex128 staging, max(N, n_z) values
   size_t bytes = 0;
+  int alloc_calls = 0;   // device allocations attempted (fault injection counts them)
   std::vector<void*> allocs;
   // accounting
   swkb_plan_stats stats{};
@@ -158,8 +167,16 @@ struct swkb_plan {
 
 namespace {
 
+// Fault injection for tests, on the host: SWKB_FAIL_ALLOC_AT=n makes the n-th
+// device allocation of a plan (counted from 1) fail as if the device were out
+// of memory, without calling cudaMalloc.
 swkb_status dev_alloc(swkb_plan* p, void** ptr, size_t bytes) {
   if (bytes == 0) bytes = 16;
+  ++p->alloc_calls;
+  if (const char* fa = getenv("SWKB_FAIL_ALLOC_AT")) {
+    if (atoi(fa) == p->alloc_calls)
+      return fail(SWKB_ERR_OOM, "device allocation %d refused (SWKB_FAIL_ALLOC_AT)", p->alloc_calls);
+  }
   cudaError_t e = cudaMalloc(ptr, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -644,6 +661,7 @@ ResumArgs<T> resum_args(const swkb_plan* p, const T* d, const T* ph, const T* a,
 
 template <typename T>
 swkb_status launch_screen(swkb_plan* p, int q, bool u_fresh) {
+  Range range("swkb_screen");
   using V = typename C2<T>::type;
   cudaStream_t s = p->stream;
   // with a two-pass DFT, pass 1 forms the field from the partials itself
@@ -749,6 +767,7 @@ swkb_status enqueue(swkb_plan* p, const double* u0, int q0, int n, double* out_d
 // sum once the rays are there.  ev_free[b] must have been recorded (set free).
 template <typename T>
 swkb_status overlapped_screen(swkb_plan* p, int q, int b, bool fresh) {
+  Range range("swkb_screen");
   using V = typename C2<T>::type;
   cudaStream_t s = p->stream, sr = p->ray_stream;
   T* rd[2] = {(T*)p->rd, (T*)p->rd1};
@@ -1393,6 +1412,7 @@ std::string tune_key(const swkb_plan* p) {
 // fastest; the choice is cached per shape for the rest of the process.
 template <typename T>
 swkb_status autotune_plan(swkb_plan* p) {
+  Range range("swkb_autotune");
   using V = typename C2<T>::type;
   const std::string key = tune_key(p);
   {
@@ -1531,6 +1551,7 @@ extern "C" {
 swkb_status swkb_plan_create(const swkb_profile* prof, double k, const swkb_domain* dom,
                              int32_t n_z, double screen_dx, const swkb_options* opt_in,
                              swkb_plan** out) {
+  Range range("swkb_plan_create");
   try {
     if (!out) return fail(SWKB_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
@@ -1597,6 +1618,7 @@ swkb_status swkb_plan_get_info(const swkb_plan* p, swkb_plan_info* info) {
 
 swkb_status swkb_propagate(swkb_plan* p, const double* u0, int32_t q0, int32_t n_screens,
                            double* u_out, int32_t snapshot_every, int32_t on_device) {
+  Range range("swkb_propagate");
   try {
     if (!p || !u0 || !u_out) return fail(SWKB_ERR_INVALID_ARG, "NULL argument");
     if (n_screens < 0 || q0 < 0) return fail(SWKB_ERR_INVALID_ARG, "negative screen count");
@@ -1627,6 +1649,7 @@ swkb_status swkb_propagate(swkb_plan* p, const double* u0, int32_t q0, int32_t n
 
 swkb_status swkb_propagate_planes(swkb_plan* p, const double* u0, int32_t q0, int32_t n_screens,
                                   int32_t planes, double* u_out, int32_t on_device) {
+  Range range("swkb_propagate_planes");
   try {
     if (!p || !u0 || !u_out) return fail(SWKB_ERR_INVALID_ARG, "NULL argument");
     if (n_screens < 0 || q0 < 0) return fail(SWKB_ERR_INVALID_ARG, "negative screen count");
