@@ -31,8 +31,15 @@ def sources():
     return sorted(f for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
-def build(verbose: bool = False, extra=()) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, extra=(), checked: bool = False) -> str:
+    """checked=True builds libswkb_checked.so with -DSWKB_BOUNDS_CHECK: device
+    indices are checked against their buffers (a violation is clamped and
+    reported as an error), the substitute for a memory sanitizer."""
+    build_dir = BUILD + ("_checked" if checked else "")
+    lib_path = LIB.replace("libswkb.so", "libswkb_checked.so") if checked else LIB
+    if checked:
+        extra = (*extra, "-DSWKB_BOUNDS_CHECK")
+    os.makedirs(build_dir, exist_ok=True)
     cc = nvcc()
     # FP32 denormals never occur on this path (deviation variables are >= 1e-12),
     # and every FP32 quotient that must be exact is a power of two done by scalbn
@@ -41,7 +48,7 @@ def build(verbose: bool = False, extra=()) -> str:
               "-I", os.path.join(ROOT, "include"), "-I", CSRC, *extra]
 
     def compile_one(src):
-        obj = os.path.join(BUILD, src[:-3] + ".o")
+        obj = os.path.join(build_dir, src[:-3] + ".o")
         cmd = [cc, *common, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -52,13 +59,13 @@ def build(verbose: bool = False, extra=()) -> str:
 
     with ThreadPoolExecutor(max_workers=max(1, len(sources()))) as ex:
         objs = list(ex.map(compile_one, sources()))
-    tmp = LIB + ".tmp"
+    tmp = lib_path + ".tmp"
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -15,6 +15,7 @@ enum : unsigned {
   ST_TURNING = 2u,   // eps - Q^2 <= 0
   ST_RANGE = 4u,     // left the permittivity table
   ST_COVER = 8u,     // ghost rays do not cover the screen
+  ST_BOUNDS = 16u,   // bounds-checked builds: a device index left its buffer
 };
 
 template <typename T> struct C2;
@@ -44,6 +45,7 @@ struct Medium {
   T z_mirror;
   T top;
   int pieces;   // FP32: > 0 when each entry is a cubic piece (4 slots), in piece units
+  long long size;   // values in coef (all columns), for bounds-checked builds
 };
 
 // Per-screen RK4 stage columns: stage l = 0 .. 2 N_t sits at x_q + l h / 2;

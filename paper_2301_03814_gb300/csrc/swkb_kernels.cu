@@ -38,6 +38,22 @@ namespace swkb {
 // ----------------------------------------------------------------------------
 // small helpers
 // ----------------------------------------------------------------------------
+// Bounds-checked builds (-DSWKB_BOUNDS_CHECK, libswkb_checked.so): an index
+// outside [0, n) sets ST_BOUNDS in the kernel's status bits, which the host
+// reports as an error, and is clamped into range so that the access stays
+// inside its buffer.  Plain builds compile the check away.
+__device__ __forceinline__ long long bchk(long long i, long long n, unsigned& st) {
+#ifdef SWKB_BOUNDS_CHECK
+  if (i < 0 || i >= n) {
+    st |= ST_BOUNDS;
+    return i < 0 ? 0 : n - 1;
+  }
+#else
+  (void)n; (void)st;
+#endif
+  return i;
+}
+
 // sin / cos of 2 pi t for |t| <= 1/2: the FP32 path uses the special-function
 // unit (absolute error ~2^-21 on [-pi, pi]); the FP64 path stays exact.
 __device__ __forceinline__ void sincos_turns(float t, float* s, float* c) {
@@ -106,7 +122,8 @@ __device__ __forceinline__ void col_eval(const Medium<T>& m, int c, T zz, T& e, 
   const int i = min(max((int)floor(u), 0), m.n_int - 1);
   const T t = u - T(i);
   T a0, a1, a2, a3, a4, a5;
-  load6<T>(m.coef + (long long)c * m.col_stride + (long long)i * 8, a0, a1, a2, a3, a4, a5);
+  load6<T>(m.coef + bchk((long long)c * m.col_stride + (long long)i * 8, m.size - 7, st), a0, a1,
+           a2, a3, a4, a5);
   // Horner with derivatives (synthetic division): p, p', p''/2 at t
   T b = a5 * t + a4;                                     // coefficient 4
   T d2 = a5;                                             // coefficient 3
@@ -214,7 +231,7 @@ __global__ void __launch_bounds__(256) k_march(const MarchArgs<T> p) {
   const T h = p.h, hh = T(0.5) * p.h, h6 = p.h / T(6);
   // landing quantities at RK4 stage l (the screen's end, or a plane inside it)
   auto land = [&](int l, T* od, T* oph, T* oa) {
-    const long long o = (long long)j * p.Mr + r;
+    const long long o = bchk((long long)j * p.Mr + r, (long long)p.NRT * p.Mr, st);
     if (!(y.Zs > T(0))) st |= ST_CAUSTIC;
     T e1, ez1, ezz1;
     medium_eval<T, MULTI>(p, l, s + y.dz, e1, ez1, ezz1, st);
@@ -338,11 +355,13 @@ __device__ __forceinline__ void med32(const MarchArgs<float>& p, int l, float u,
   const int i = (int)(__float_as_uint(v) - 0x4B400000u);
   const float t = uc - (v - 12582912.f);
   if (!MULTI) {
-    table_eval<CUBIC>(p.med.coef + (long long)i * W, t, e, d1, d2);
+    table_eval<CUBIC>(p.med.coef + bchk((long long)i * W, p.med.size - (W - 1), st), t, e, d1, d2);
   } else {
     const int c = __ldg(p.st.c + l);
     const float th = __ldg(p.st.th + l);
-    const float* q = p.med.coef + (long long)c * p.med.col_stride + (long long)i * W;
+    const float* q = p.med.coef + bchk((long long)c * p.med.col_stride + (long long)i * W,
+                                       p.med.size - (th == 0.f ? W - 1 : p.med.col_stride + W - 1),
+                                       st);
     if (th == 0.f) {
       table_eval<CUBIC>(q, t, e, d1, d2);
     } else if (th == 1.f) {
@@ -443,7 +462,9 @@ __global__ void __launch_bounds__(256) k_march_x2(const MarchArgs<float> p) {
   const auto pos = [&](const Ray2& w) { return fma2(w.dz, ih, s); };
   // landing quantities at RK4 stage l (the screen's end, or a plane inside it)
   const auto land = [&](int l, float* od, float* oph, float* oam) {
-    const long long oa = (long long)ja * p.Mr + r, ob = (long long)jb * p.Mr + r;
+    const long long nrm = (long long)p.NRT * p.Mr;
+    const long long oa = bchk((long long)ja * p.Mr + r, nrm, st);
+    const long long ob = has_b ? bchk((long long)jb * p.Mr + r, nrm, st) : oa;
     float dza, dzb, dQa, dQb, rha, rhb, Zsa, Zsb, u1a, u1b;
     sp2(y.dz, dza, dzb);
     sp2(y.dQ, dQa, dQb);
@@ -539,7 +560,8 @@ __device__ __forceinline__ unsigned bracket_pair(const BracketArgs<T>& p, int i,
     for (int k = 0; k < 4 && T((t1 + 1) * TM - b1) < d1; ++k) ++t1;
     t0 = max(t0, 0);
     t1 = min(t1, p.n_tiles);
-    for (int t = t0; t <= t1; ++t) p.jlo[(long long)t * p.Mr + i] = j;
+    for (int t = t0; t <= t1; ++t)
+      p.jlo[bchk((long long)t * p.Mr + i, (long long)(p.n_tiles + 1) * p.Mr, st)] = j;
   }
   if (p.sym) {
     // mirror family: its bracket of tile start t TM is ray NRT - 1 - j when
@@ -555,9 +577,11 @@ __device__ __forceinline__ unsigned bracket_pair(const BracketArgs<T>& p, int i,
     for (int k = 0; k < 4 && d0 < T(p.N - (t1 + 1) * TM - b0); ++k) ++t1;
     t0 = max(t0, 0);
     t1 = min(t1, p.n_tiles);
-    for (int t = t0; t <= t1; ++t) p.jlo_neg[(long long)t * p.Mr + i] = p.NRT - 1 - j;
+    for (int t = t0; t <= t1; ++t)
+      p.jlo_neg[bchk((long long)t * p.Mr + i, (long long)(p.n_tiles + 1) * p.Mr, st)] =
+          p.NRT - 1 - j;
   }
-  return 0;
+  return st;
 }
 
 // One thread per landing pair (measured faster than longer per-thread runs:
@@ -571,12 +595,15 @@ __global__ void k_bracket(const BracketArgs<T> p) {
   if (i >= p.Mr) return;
   const int j1 = min(j0 + BRACKET_RUN, p.NRT - 1);   // pairs (j, j + 1), j < j1
   unsigned st = 0;
-  T d0 = p.d[(long long)j0 * p.Mr + i];
+  unsigned bst = 0;
+  const long long nrm = (long long)p.NRT * p.Mr;
+  T d0 = p.d[bchk((long long)j0 * p.Mr + i, nrm, bst)];
   for (int j = j0; j < j1; ++j) {
-    const T d1 = p.d[(long long)(j + 1) * p.Mr + i];
+    const T d1 = p.d[bchk((long long)(j + 1) * p.Mr + i, nrm, bst)];
     st |= bracket_pair(p, i, j, d0, d1);
     d0 = d1;
   }
+  st |= bst;
   if (st) atomicOr(p.status, st);
 }
 
@@ -720,8 +747,9 @@ __global__ void __launch_bounds__(RESUM_WARPS * 32, sizeof(T) == 4 ? 7 : 1) k_re
     bool mir;
     const int col = column(i, mir);
     const int* jt = mir ? p.jlo_neg : p.jlo;
-    jl = __ldg(jt + (long long)tile * p.Mr + col);
-    jh = __ldg(jt + (long long)(tile + 1) * p.Mr + col);
+    const long long nj = (long long)(p.n_tiles + 1) * p.Mr;
+    jl = __ldg(jt + bchk((long long)tile * p.Mr + col, nj, st));
+    jh = __ldg(jt + bchk((long long)(tile + 1) * p.Mr + col, nj, st));
   };
   // A bracket table left inconsistent by a failed screen (already flagged by
   // k_bracket) must not send the reads out of [0, NRT); a window wider than
@@ -744,7 +772,8 @@ __global__ void __launch_bounds__(RESUM_WARPS * 32, sizeof(T) == 4 ? 7 : 1) k_re
     for (int r = 0; r < PF; ++r) {
       const int w = lane + 32 * r;
       if (w < W) {
-        const long long o = (long long)ray_of(mir, jb, w) * p.Mr + col;
+        const long long o = bchk((long long)ray_of(mir, jb, w) * p.Mr + col,
+                                 (long long)p.NRT * p.Mr, st);
         rd[r] = __ldg(p.d + o);
         rph[r] = __ldg(p.ph + o);
         ra[r] = __ldg(p.a + o);
@@ -781,7 +810,8 @@ __global__ void __launch_bounds__(RESUM_WARPS * 32, sizeof(T) == 4 ? 7 : 1) k_re
         }
       }
       for (int w = lane + 32 * PF; w < W; w += 32) {   // beyond the prefetched rounds
-        const long long o = (long long)ray_of(mirrored, jb, w) * p.Mr + col;
+        const long long o = bchk((long long)ray_of(mirrored, jb, w) * p.Mr + col,
+                                 (long long)p.NRT * p.Mr, st);
         s_X[w] = T(base + w * p.R) + dsign * __ldg(p.d + o);
         s_ph[w] = __ldg(p.ph + o);
         s_a[w] = __ldg(p.a + o);
@@ -842,7 +872,6 @@ __global__ void __launch_bounds__(RESUM_WARPS * 32, sizeof(T) == 4 ? 7 : 1) k_re
       nm = (nm + nn) & mask;
     }
   }
-  if (st) atomicOr(p.status, st);
   // fixed-order sum of the warps' partial sums
   __syncthreads();
   // per warp TM points as 32 runs of PW, each run padded to PW + 1 entries so
@@ -857,7 +886,8 @@ __global__ void __launch_bounds__(RESUM_WARPS * 32, sizeof(T) == 4 ? 7 : 1) k_re
     red[warp * TMP + lane * (PW + 1) + q] = v;
   }
   __syncthreads();
-  V* out = p.part + (long long)group * p.N + m0;
+  V* out = p.part + bchk((long long)group * p.N + m0, (long long)p.n_groups * p.N - (TM - 1), st);
+  if (st) atomicOr(p.status, st);
   for (int x = threadIdx.x; x < TM; x += blockDim.x) {
     const int xs = (x / PW) * (PW + 1) + x % PW;
     V sum = red[xs];

@@ -216,6 +216,8 @@ swkb_status upload(swkb_plan* p, void** dst, const std::vector<double>& v) {
 }
 
 swkb_status status_from_bits(unsigned bits) {
+  if (bits & ST_BOUNDS)
+    return fail(SWKB_ERR_CUDA, "a device index left its buffer (bounds-checked build)");
   if (bits & ST_CAUSTIC)
     return fail(SWKB_ERR_CAUSTIC,
                 "caustic between screens (Z_s <= 0 or ray landings out of order); "
@@ -597,6 +599,7 @@ MarchArgs<T> march_args(const swkb_plan* p, int q) {
   a.med.z_mirror = (T)p->z_a;
   a.med.top = (T)p->n_int;
   a.med.pieces = 0;
+  a.med.size = (long long)p->n_cols * p->n_int * 8;
   if (sizeof(T) == 4) {
     // reflection stored in the table; positions in table intervals
     const double z0 = p->mirror ? p->z0p - p->n_int * p->dzp : p->z0p;
@@ -610,6 +613,7 @@ MarchArgs<T> march_args(const swkb_plan* p, int q) {
     a.med.inv_h2 = (T)(2.0 / (hs * hs));
     a.med.mirrored = 0;
     a.med.pieces = p->pieces;
+    a.med.size = (long long)p->n_cols * a.med.col_stride;
     a.med.top = (T)a.med.n_int;
     a.u_lo = (T)((p->z_lo - z0) / hs);
     a.u_dz = (T)(p->dz / hs);

@@ -97,12 +97,16 @@ _lib = None
 
 
 def lib():
-    """Load the in-tree libswkb.so (raises if it has not been built)."""
+    """Load the in-tree libswkb.so (raises if it has not been built).
+    SWKB_CHECKED=1 loads the bounds-checked build libswkb_checked.so instead."""
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB_PATH):
-            raise ImportError(f"{LIB_PATH} is missing: build it with paper_2301_03814_gb300.build")
-        L = ctypes.CDLL(LIB_PATH)
+        path = LIB_PATH
+        if os.environ.get("SWKB_CHECKED") == "1":
+            path = LIB_PATH.replace("libswkb.so", "libswkb_checked.so")
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is missing: build it with paper_2301_03814_gb300.build")
+        L = ctypes.CDLL(path)
         L.swkb_options_default.argtypes = [POINTER(swkb_options)]
         L.swkb_options_default.restype = None
         L.swkb_plan_create.argtypes = [POINTER(swkb_profile), c_double, POINTER(swkb_domain),
