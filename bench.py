@@ -118,11 +118,14 @@ def run_reference(args, rank, world):
         ts.append(dt * m_all / m_used)
     t_screen = statistics.mean(ts)
     value = pb.n_z / t_screen
-    line = {"impl": "reference", "metric": METRIC.replace("mixed FP32/FP64 path", "CPU oracle"),
+    # the same metric and config as the GPU arm's line (the sample is in cpu_baseline)
+    line = {"impl": "reference", "metric": METRIC,
             "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": statistics.mean(raw) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_dict(pb, {"sample_screens_per_step": 1}),
+            "data": "synthetic",
+            "config": config_dict(pb, {"parallelism": f"replicas x{world}" if world > 1
+                                       else "single GPU"}),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"each step: 1 screen over every {ORACLE_MODE_STRIDE}th "
                                        f"mode, scaled by the mode count"},
