@@ -164,3 +164,34 @@ def test_uneven_batch_mixed_matches_fp64():
         assert sa == swkb.SWKB_OK and sb == swkb.SWKB_OK, swkb.swkb_last_error()
         assert rel_l2(ua, ub) < 1e-4, pb.name
     srv.close()
+
+
+def test_concurrent_submitters_and_pollers():
+    # four host threads submit and poll at the same time (the server is
+    # thread-safe); every result equals the request run alone
+    jobs = mix()
+    alone = {i: swkb.Plan(pb, prec).propagate() for i, (pb, prec) in enumerate(jobs)}
+    srv = swkb.Server(8 * GB, max_slots=3)
+    errors = []
+
+    def worker(ids):
+        try:
+            for i in ids:
+                pb, prec = jobs[i]
+                st, t = srv.submit(pb, prec)
+                assert st == swkb.SWKB_OK
+                st, got = srv.poll(t, timeout_ms=120_000)
+                assert st == swkb.SWKB_OK
+                assert np.array_equal(got, alone[i])
+        except AssertionError as e:       # reported in the main thread
+            errors.append(e)
+    threads = [threading.Thread(target=worker, args=([i, (i + 2) % len(jobs)],))
+               for i in range(4)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    s = srv.stats()
+    srv.close()
+    assert not errors, errors
+    assert s["completed"] == 8 and s["failed"] == 0
