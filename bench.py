@@ -56,6 +56,10 @@ def parse_args():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="default launch shapes instead of the autotuned ones (for profiling)")
+    ap.add_argument("--tiling", default=None, metavar="TILE,CTAS,N1",
+                    help="fixed launch shapes of the mixed plan (tile_points, ctas_per_sm, "
+                         "fft_n1, as the JSON line's \"tiling\" reports them) instead of "
+                         "autotuning: a profiler run then times the shapes a plain run chose")
     ap.add_argument("--large", action="store_true",
                     help="instead of the benchmark, time the paper-scale range-dependent duct "
                          "and the full uneven batch once (one JSON line; minutes)")
@@ -358,9 +362,12 @@ def run_ours(args, world, rank, local):
         dist.init_process_group("nccl")
     pb = workload()
     stream = torch.cuda.Stream(device=dev)
-    tune = not args.no_autotune
-    plan = swkb.Plan(pb, swkb.SWKB_MIXED, stream=stream.cuda_stream, device=local, autotune=tune)
-    plan64 = swkb.Plan(pb, swkb.SWKB_FP64, stream=stream.cuda_stream, device=local, autotune=tune)
+    tune = not args.no_autotune and args.tiling is None
+    fixed = tuple(int(v) for v in args.tiling.split(",")) if args.tiling else None
+    plan = swkb.Plan(pb, swkb.SWKB_MIXED, stream=stream.cuda_stream, device=local, autotune=tune,
+                     tiling=fixed)
+    plan64 = swkb.Plan(pb, swkb.SWKB_FP64, stream=stream.cuda_stream, device=local,
+                       autotune=not args.no_autotune)
     u0 = torch.from_numpy(pb.u0).to(dev)
     out = torch.empty_like(u0)
     out64 = torch.empty_like(u0)
@@ -385,8 +392,9 @@ def run_ours(args, world, rank, local):
         return ts
 
     # per-kernel breakdown: one extra step (not part of the headline) with
-    # CUDA events around every launch
-    plan.set_timing(True)
+    # CUDA events around every launch and the march on the plan's stream, so
+    # that each event pair brackets one kernel with the GPU to itself
+    plan.set_timing(True, serial=True)
     timed(plan, out, 2)
     breakdown = plan.stats()
     kms_all = {k: v / 2 for k, v in breakdown["kernel_ms"].items()}   # per step
@@ -498,15 +506,17 @@ def run_ours(args, world, rank, local):
             "data": "synthetic",
             "config": config_dict(pb, {"parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
             "e2e": e2e, "gpu_launches": int(st["launches"]),
-            "tiling": {"tile_points": info.tile_points, "mode_groups": info.mode_groups,
-                       "fft_n1": info.fft_n1, "autotuned": tune},
+            "tiling": {"tile_points": info.tile_points, "ctas_per_sm": info.ctas_per_sm,
+                       "mode_groups": info.mode_groups, "fft_n1": info.fft_n1,
+                       "autotuned": tune},
             "fp64": {"value": value64, "unit": UNIT, "ms_per_step": statistics.mean(ts64),
                      "steps": len(ts64), "kernel_ms_per_step": {k: v / len(ts64) for k, v in st64["kernel_ms"].items()},
                      "march_roofline": fp64_roof},
             "mixed_vs_fp64_rel_l2": err,
             "x_invariant_ray_reuse": reuse,
             "kernel_ms_per_step": kms_all,
-            "kernel_ms_per_step_note": "one extra step with events around every launch",
+            "kernel_ms_per_step_note": "one extra step, march serialised onto the plan stream, "
+                                       "events around every launch",
             "kernel_share": share, "roofline": roofline, "clocks": clk,
             "step_ms": {"p50": statistics.median(ts), "p99": float(np.percentile(ts, 99)),
                         "min": min(ts), "max": max(ts)}}

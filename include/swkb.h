@@ -126,6 +126,18 @@ typedef struct {
                              for P - 1 planes inside each screen, enabling
                              swkb_propagate_planes with up to P planes per
                              screen (0 or 1 = none)                           */
+  /* Fixed launch shapes, e.g. those an autotuned plan reported in
+     swkb_plan_info.  All three > 0 replaces the default and the autotuned
+     shapes (autotune is then skipped): tile_points in {64, 128, 256, 512}
+     and at most the summed period (n_fft, or n_fft / 2 when grounded);
+     ctas_per_sm >= 1; fft_n1 a power of two, at most 64 and n_fft / 32.
+     Otherwise SWKB_ERR_INVALID_ARG.  All three 0 = default or autotuned
+     shapes.  The shapes change the launch layout and the order of some
+     sums (the DFT split, the mode groups' partial sums), so fields differ
+     between shapes by rounding only. */
+  int32_t tile_points;    /* grid points per resummation tile                 */
+  int32_t ctas_per_sm;    /* resummation CTAs per SM the mode groups target   */
+  int32_t fft_n1;         /* DFT split N = fft_n1 * (N / fft_n1)              */
 } swkb_options;
 
 typedef struct {
@@ -147,6 +159,7 @@ typedef struct {
   int32_t medium_pieces;  /* FP32 plans: cubic pieces per permittivity-table
                              interval the march evaluates (0: the quintic
                              itself; always 0 for FP64 plans)                 */
+  int32_t ctas_per_sm;    /* resummation CTAs per SM the mode groups target  */
 } swkb_plan_info;
 
 /* Fill *opt with defaults: FP64, theta_max 30 deg, R 1, N_t 8, no absorber. */
@@ -247,8 +260,13 @@ typedef struct {
    every kind, 0 to stop) whose launches get CUDA events recorded around them
    on the plan's stream, accumulating per-kind device time; every >= 1 times
    one launch in `every` of each selected kind (each timed launch adds two
-   event records to the stream).  Resets the counters. */
+   event records to the stream).  Resets the counters.  With SWKB_TIME_SERIAL
+   or'ed into kinds, swkb_propagate runs the ray march on the plan's stream
+   as well (no second stream), so that each event pair brackets its own
+   kernel alone instead of a kernel sharing the GPU with the march; the
+   results are bit-identical either way. */
 #define SWKB_TIME_ALL ((1 << SWKB_KERNEL_KINDS) - 1)
+#define SWKB_TIME_SERIAL (1 << 30)
 swkb_status swkb_plan_set_timing(swkb_plan* plan, int32_t kinds, int32_t every);
 swkb_status swkb_plan_get_stats(const swkb_plan* plan, swkb_plan_stats* stats);
 

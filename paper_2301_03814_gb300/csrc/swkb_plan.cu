@@ -136,6 +136,7 @@ struct swkb_plan {
   swkb_plan_stats stats{};
   unsigned timing = 0;               // bit k: time kernel kind k with CUDA events
   int timing_every = 1;              // time one launch in timing_every per kind
+  bool timing_serial = false;        // while timing: march on the plan stream too
   uint64_t timing_seen[SWKB_KERNEL_KINDS] = {};
   std::vector<cudaEvent_t> events;   // pool, reused every run
   struct Mark { int kind; int e0, e1; };
@@ -543,6 +544,12 @@ swkb_status event_at(swkb_plan* p, int idx) {
   }
   return SWKB_OK;
 }
+
+// propagate calls run the march on the ray stream unless the plan has none or
+// serial timing is on
+bool overlapped(const swkb_plan* p) { return p->overlap && !p->timing_serial; }
+
+int timing_key(const swkb_plan* p) { return (int)p->timing | (p->timing_serial ? SWKB_TIME_SERIAL : 0); }
 
 template <typename F>
 swkb_status timed_on(swkb_plan* p, cudaStream_t stream, int kind, int n_launches, F&& launch) {
@@ -975,15 +982,15 @@ swkb_status run_graph(swkb_plan* p, const double* u0, int q0, int n, double* dst
   swkb_plan::Graph* g = nullptr;
   for (auto& e : p->graphs)
     if (e.q0 == q0 && e.n == n && e.snap == snap && e.in == u0 && e.out == dst &&
-        e.timing == (int)p->timing && e.every == p->timing_every)
+        e.timing == timing_key(p) && e.every == p->timing_every)
       g = &e;
   if (!g) {
     if (p->graphs.size() >= 8) drop_graphs(p);
     const swkb_plan_stats before = p->stats;
     p->marks.clear();
     CK(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
-    swkb_status st = p->overlap ? enqueue_overlapped<T>(p, u0, q0, n, dst, nullptr, snap)
-                                : enqueue<T>(p, u0, q0, n, dst, nullptr, snap);
+    swkb_status st = overlapped(p) ? enqueue_overlapped<T>(p, u0, q0, n, dst, nullptr, snap)
+                                   : enqueue<T>(p, u0, q0, n, dst, nullptr, snap);
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(p->stream, &graph);
     if (st == SWKB_OK && ec != cudaSuccess)
@@ -995,7 +1002,7 @@ swkb_status run_graph(swkb_plan* p, const double* u0, int q0, int n, double* dst
         st = fail(SWKB_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(ei));
     }
     if (graph) cudaGraphDestroy(graph);
-    swkb_plan::Graph e{q0, n, snap, (int)p->timing, p->timing_every, u0, dst, exec, p->marks, {}};
+    swkb_plan::Graph e{q0, n, snap, timing_key(p), p->timing_every, u0, dst, exec, p->marks, {}};
     e.delta.launches = p->stats.launches - before.launches;
     e.delta.screens = p->stats.screens - before.screens;
     for (int kk = 0; kk < SWKB_KERNEL_KINDS; ++kk) {
@@ -1035,8 +1042,8 @@ swkb_status run(swkb_plan* p, const double* u0, int q0, int n, double* out_dev, 
                          p->stream));
     return read_status(p);
   }
-  TRY(p->overlap ? enqueue_overlapped<T>(p, u0, q0, n, out_dev, out_host, snap)
-                 : enqueue<T>(p, u0, q0, n, out_dev, out_host, snap));
+  TRY(overlapped(p) ? enqueue_overlapped<T>(p, u0, q0, n, out_dev, out_host, snap)
+                    : enqueue<T>(p, u0, q0, n, out_dev, out_host, snap));
   return read_status(p);
 }
 
@@ -1335,8 +1342,26 @@ swkb_status configure(swkb_plan* p, const swkb_profile* prof, double k, const sw
   p->planes = opt.planes > 1 ? opt.planes : 0;
   if (p->planes && (p->planes > p->Nt || p->Nt % p->planes))
     return fail(SWKB_ERR_INVALID_ARG, "planes (%d) must divide rk4_steps (%d)", p->planes, p->Nt);
-  const Tiling def = default_tiling(p);
+  Tiling def = default_tiling(p);
+  if (opt.tile_points != 0 || opt.ctas_per_sm != 0 || opt.fft_n1 != 0) {
+    const Tiling t{opt.tile_points / 32, opt.ctas_per_sm, opt.fft_n1};
+    if (opt.tile_points % 32 || opt.ctas_per_sm > 1024 || !valid_tiling(p, t))
+      return fail(SWKB_ERR_INVALID_ARG,
+                  "launch shapes (tile_points %d, ctas_per_sm %d, fft_n1 %d) are not valid for "
+                  "this plan", opt.tile_points, opt.ctas_per_sm, opt.fft_n1);
+    def = t;
+    p->autotune = false;
+  }
   apply_tiling(p, def);
+  {
+    int optin = 0;
+    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
+    const size_t smem = p->precision == SWKB_FP64 ? resum_smem_bytes<double>(p->wcap, p->TM)
+                                                  : resum_smem_bytes<float>(p->wcap, p->TM);
+    if (smem > (size_t)optin)
+      return fail(SWKB_ERR_INVALID_ARG, "resummation tile of %d points needs %zu B of shared "
+                  "memory (%d available)", p->TM, smem, optin);
+  }
   p->alloc_groups = p->n_groups;
   p->alloc_tiles = p->n_tiles;
   if (p->autotune) {
@@ -1617,6 +1642,7 @@ swkb_status swkb_plan_get_info(const swkb_plan* p, swkb_plan_info* info) {
   info->eps_ref = p->eps_ref;
   info->device_bytes = p->bytes;
   info->medium_pieces = p->pieces;
+  info->ctas_per_sm = p->ctas_per_sm;
   return SWKB_OK;
 }
 
@@ -1702,6 +1728,7 @@ swkb_status swkb_plan_set_timing(swkb_plan* p, int32_t kinds, int32_t every) {
   if (!p) return fail(SWKB_ERR_INVALID_ARG, "NULL plan");
   if (every < 1) return fail(SWKB_ERR_INVALID_ARG, "every must be >= 1");
   p->timing = (unsigned)kinds & ((1u << SWKB_KERNEL_KINDS) - 1u);
+  p->timing_serial = p->timing != 0 && (kinds & SWKB_TIME_SERIAL) != 0;
   p->timing_every = every;
   memset(p->timing_seen, 0, sizeof(p->timing_seen));
   p->marks.clear();

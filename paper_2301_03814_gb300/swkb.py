@@ -61,7 +61,8 @@ class swkb_options(ctypes.Structure):
     _fields_ = [("precision", c_int32), ("theta_max", c_double), ("n_max", c_int32),
                 ("ray_stride", c_int32), ("rk4_steps", c_int32), ("absorber_frac", c_double),
                 ("autotune", c_int32), ("cuda_stream", c_void_p), ("device", c_int32),
-                ("reuse_rays", c_int32), ("planes", c_int32)]
+                ("reuse_rays", c_int32), ("planes", c_int32), ("tile_points", c_int32),
+                ("ctas_per_sm", c_int32), ("fft_n1", c_int32)]
 
 
 class swkb_plan_info(ctypes.Structure):
@@ -70,7 +71,7 @@ class swkb_plan_info(ctypes.Structure):
                 ("tile_points", c_int32), ("mode_groups", c_int32), ("march_modes", c_int32),
                 ("resum_points", c_int32), ("fft_n1", c_int32), ("dz", c_double),
                 ("period", c_double), ("eps_ref", c_double), ("device_bytes", c_size_t),
-                ("medium_pieces", c_int32)]
+                ("medium_pieces", c_int32), ("ctas_per_sm", c_int32)]
 
 
 class swkb_plan_stats(ctypes.Structure):
@@ -187,7 +188,9 @@ def swkb_options_default() -> swkb_options:
 
 
 def options_for(problem, precision=SWKB_FP64, stream=None, device=0, autotune=False,
-                reuse_rays=False, planes=0) -> swkb_options:
+                reuse_rays=False, planes=0, tiling=None) -> swkb_options:
+    """tiling: None, or fixed launch shapes (tile_points, ctas_per_sm, fft_n1)
+    as swkb_plan_info reports them."""
     o = swkb_options_default()
     o.precision = precision
     o.theta_max = float(problem.theta_max)
@@ -200,6 +203,8 @@ def options_for(problem, precision=SWKB_FP64, stream=None, device=0, autotune=Fa
     o.autotune = 1 if autotune else 0
     o.reuse_rays = 1 if reuse_rays else 0
     o.planes = int(planes)
+    if tiling is not None:
+        o.tile_points, o.ctas_per_sm, o.fft_n1 = (int(v) for v in tiling)
     return o
 
 
@@ -243,12 +248,14 @@ def swkb_plan_destroy(plan):
 
 
 TIME_ALL = (1 << len(KERNEL_KINDS)) - 1
+TIME_SERIAL = 1 << 30
 
 
-def swkb_plan_set_timing(plan, kinds, every=1):
+def swkb_plan_set_timing(plan, kinds, every=1, serial=False):
     """kinds: True (all kernel kinds), False (off), or an int bit mask /
     an iterable of kind names ("march", "resum", ...); every: time one launch
-    in `every` of each selected kind."""
+    in `every` of each selected kind; serial: march on the plan's stream too,
+    so that each timed launch has the GPU to itself."""
     if kinds is True:
         mask = TIME_ALL
     elif kinds is False or kinds is None:
@@ -259,6 +266,8 @@ def swkb_plan_set_timing(plan, kinds, every=1):
         mask = 0
         for k in kinds:
             mask |= 1 << KERNEL_KINDS.index(k)
+    if serial:
+        mask |= TIME_SERIAL
     check(lib().swkb_plan_set_timing(plan, int(mask), int(every)))
 
 
@@ -368,11 +377,11 @@ class Plan:
     """A plan for one workloads.Problem (or equivalent fields)."""
 
     def __init__(self, problem, precision=SWKB_FP64, stream=None, device=0, autotune=False,
-                 reuse_rays=False, planes=0):
+                 reuse_rays=False, planes=0, tiling=None):
         self.problem = problem
         dom = swkb_domain(problem.z_a, problem.z_b, problem.x0, problem.bc)
         self.options = options_for(problem, precision, stream, device, autotune, reuse_rays,
-                                   planes)
+                                   planes, tiling)
         self.handle = swkb_plan_create(problem.profile, problem.k, dom, problem.n_z,
                                        problem.dx, self.options)
         self.info = swkb_plan_get_info(self.handle)
@@ -423,8 +432,8 @@ class Plan:
             n_screens = self.problem.n_screens
         return swkb_propagate_planes(self.handle, u0_ptr, q0, n_screens, planes, out_ptr, 1)
 
-    def set_timing(self, kinds=True, every=1):
-        swkb_plan_set_timing(self.handle, kinds, every)
+    def set_timing(self, kinds=True, every=1, serial=False):
+        swkb_plan_set_timing(self.handle, kinds, every, serial)
 
     def stats(self) -> dict:
         return swkb_plan_get_stats(self.handle)

@@ -279,6 +279,60 @@ def test_autotuned_plan_parity(prec, tol):
     assert rel_l2(plan.propagate(), duct_small_oracle()) < tol
 
 
+@pytest.mark.parametrize("prec,tol", [(swkb.SWKB_FP64, FP64_TOL), (swkb.SWKB_MIXED, MIXED_TOL)])
+def test_fixed_launch_shapes(prec, tol):
+    """Launch shapes an autotuned plan reports, given back as fixed shapes,
+    rebuild the same plan without timing anything (bit-identical fields);
+    other valid shapes still match the oracle; invalid ones are refused."""
+    pb = duct_small()
+    tuned = swkb.Plan(pb, prec, autotune=True)
+    i = tuned.info
+    shapes = (i.tile_points, i.ctas_per_sm, i.fft_n1)
+    fixed = swkb.Plan(pb, prec, tiling=shapes)
+    assert (fixed.info.tile_points, fixed.info.ctas_per_sm, fixed.info.fft_n1) == shapes
+    assert fixed.info.mode_groups == i.mode_groups
+    assert np.array_equal(fixed.propagate(), tuned.propagate())
+    n = fixed.info.n_fft
+    for sh in [(64, 1, 1), (128, 12, 2), (512, 3, min(64, n // 32))]:
+        plan = swkb.Plan(pb, prec, tiling=sh)
+        assert (plan.info.tile_points, plan.info.ctas_per_sm, plan.info.fft_n1) == sh
+        assert rel_l2(plan.propagate(), duct_small_oracle()) < tol
+    for bad in [(96, 4, 1), (1024, 4, 1), (128, 0, 1), (128, 4, 3), (128, 4, 128),
+                (128, 4, 0), (0, 4, 2)]:
+        with pytest.raises(swkb.SwkbError) as e:
+            swkb.Plan(pb, prec, tiling=bad)
+        assert e.value.status == swkb.SWKB_ERR_INVALID_ARG, bad
+
+
+@pytest.mark.parametrize("prec", [swkb.SWKB_FP64, swkb.SWKB_MIXED])
+def test_serial_timing(prec):
+    """With serial timing the march runs on the plan's stream: same field, and
+    the per-kernel event times of one propagation add up to no more than its
+    wall time on the device."""
+    torch = pytest.importorskip("torch")
+    pb = duct_small()
+    want = swkb.Plan(pb, prec).propagate()
+    s = torch.cuda.Stream()
+    plan = swkb.Plan(pb, prec, stream=s.cuda_stream)
+    plan.set_timing(True, serial=True)
+    u0 = torch.from_numpy(pb.u0).cuda()
+    out = torch.empty_like(u0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    plan.propagate_device(u0.data_ptr(), out.data_ptr())   # graph capture
+    plan.set_timing(True, serial=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    plan.propagate_device(u0.data_ptr(), out.data_ptr())
+    e1.record(s)
+    torch.cuda.synchronize()
+    st = plan.stats()
+    assert np.array_equal(out.cpu().numpy(), want)
+    assert st["kernel_timed"]["march"] == pb.n_screens
+    total = sum(st["kernel_ms"].values())
+    assert 0 < total <= e0.elapsed_time(e1) * 1.02 + 0.05
+    plan.set_timing(False)
+
+
 @pytest.mark.parametrize("prec", [swkb.SWKB_FP64, swkb.SWKB_MIXED])
 def test_reuse_rays_identical_for_range_independent_media(prec):
     """The ray data depend only on the medium slab: with one table column,
