@@ -351,6 +351,50 @@ def batched_measurement(swkb, n=64, screens=10, seed=4):
             "draw": "C4: f U(1,10) GHz, H U(100,400) m, N_z 2^12..2^16, seed 4"}
 
 
+def sov_measurement(swkb, dev, with_oracle):
+    """The separation-of-variables reference (Sec. 3.1) on the GPU: FP64
+    Galerkin matrices, batched Jacobi eigen-solve, projection and advance,
+    timed with CUDA events around swkb_hill_propagate on device buffers (one
+    warm-up call first).  The oracle (numpy / LAPACK, one call) is timed
+    beside it as the CPU baseline of this workload."""
+    import torch
+    from paper_2301_03814_gb300 import workloads as w
+    out = {}
+    for name, hi in (("gaussian_duct_200km", w.hill_gaussian_duct_200km()),
+                     ("surface_duct_2km", w.hill_surface_duct_2km()),
+                     ("surface_duct_2km_batch8", w.hill_surface_duct_2km(batch=8))):
+        d = swkb.hill_desc(hi.bc, hi.z_a, hi.z_b, hi.n_z, hi.K, hi.n_q, z_sym=hi.z_c)
+        eps = torch.from_numpy(hi.eps).to(dev)
+        u0 = torch.from_numpy(hi.u0).to(dev)
+        res = torch.empty((len(hi.k), len(hi.xs), hi.n_z), dtype=torch.complex128, device=dev)
+        stream = torch.cuda.Stream(device=dev)
+        swkb.swkb_hill_propagate_device(d, hi.k, eps.data_ptr(), u0.data_ptr(), hi.xs,
+                                        res.data_ptr(), None, stream.cuda_stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e0.record(stream)
+        swkb.swkb_hill_propagate_device(d, hi.k, eps.data_ptr(), u0.data_ptr(), hi.xs,
+                                        res.data_ptr(), None, stream.cuda_stream)
+        e1.record(stream)
+        e1.synchronize()
+        wall = time.perf_counter() - t0
+        n_mat = len(hi.k) * (2 if hi.bc == swkb.SWKB_BC_PERIODIC else 1)
+        rec = {"workload": hi.name, "problems": len(hi.k), "K": hi.K, "n_q": hi.n_q,
+               "matrices": n_mat, "matrix_size": hi.K + 1, "ms": e0.elapsed_time(e1),
+               "wall_ms": wall * 1e3}
+        if with_oracle and len(hi.k) == 1:
+            from oracle import hill_oracle
+            t0 = time.perf_counter()
+            hill_oracle.propagate(hi.k[0], hi.eps[0], hi.u0[0], hi.xs, hi.bc, hi.z_a, hi.z_b,
+                                  hi.K, z_c=hi.z_c)
+            rec["cpu_baseline"] = {"ms": (time.perf_counter() - t0) * 1e3, "kind": "oracle",
+                                   "cores": os.cpu_count(),
+                                   "note": "numpy with its BLAS/LAPACK default thread pool"}
+        out[name] = rec
+    return out
+
+
 def run_ours(args, world, rank, local):
     import torch
     from paper_2301_03814_gb300 import swkb
@@ -524,6 +568,8 @@ def run_ours(args, world, rank, local):
         line["serving"] = serving_measurement(swkb)
         line["serving_sweep"] = serving_sweep(swkb)
         line["batched"] = batched_measurement(swkb)
+    if world == 1 and not args.no_serving:
+        line["sov_reference"] = sov_measurement(swkb, dev, not args.no_cpu_baseline)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(pb)
     print(json.dumps(line), flush=True)

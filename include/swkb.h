@@ -339,6 +339,82 @@ swkb_status swkb_server_get_stats(swkb_server* server, swkb_server_stats* stats)
 /* Cancels queued requests, waits for resident ones, frees everything. */
 void swkb_server_destroy(swkb_server* server);
 
+/* ---------------------------------------------------------------------------
+ * Separation-of-variables reference (Sec. 3.1).  For a permittivity that
+ * does not depend on x, the exact one-way field is u(x, z) = sum_i a_i
+ * exp(i alpha_i x) phi_i(z) (Eq. series_sol), with (phi_i, alpha_i^2) the
+ * eigenpairs of the Sturm-Liouville problem phi'' + k^2 eps phi =
+ * alpha^2 phi (Eq. phi_equation) and a_i the projections of the field at
+ * x = 0 (Eqs. series_init, sl_expansion).  The library discretises it by
+ * Galerkin on the Fourier modes |n| <= K of the period, split by parity about
+ * a symmetry point z_c of eps: in the orthonormal bases 1, sqrt(2)
+ * cos(kappa_n s) (n = 1..K) and sqrt(2) sin(kappa_n s) (n = 1..K),
+ * s = z - z_c, kappa_n = 2 pi n / L, the operator is the real symmetric
+ * matrix A_nm = -kappa_n^2 delta_nm + k^2 w_n w_m (eh_|n-m| +- eh_(n+m)) / 2
+ * (w_0 = 1, w_n = sqrt(2); + cosines, - sines; eh_j the period mean of
+ * eps cos(kappa_j s)), whose eigenpairs come from a batched FP64 Jacobi
+ * eigen-solver.  alpha_i is the principal square root (evanescent modes
+ * decay).
+ * ------------------------------------------------------------------------- */
+
+/*
+ * Batched eigen-decomposition of real symmetric matrices, FP64, by the
+ * parallel cyclic Jacobi method (round-robin pairing: every sweep rotates
+ * each index pair once, n/2 disjoint pairs at a time, on the device).
+ * A: batch matrices of n x n, row-major; (A + A^T) / 2 is decomposed.
+ * lambda_out: batch x n eigenvalues, in no particular order.
+ * vectors_out: batch x n x n, row j the unit eigenvector of lambda_out[j]
+ * (NULL: not returned).  sweeps_out (NULL: not returned): sweeps used, the
+ * largest over the batch; the iteration stops once the off-diagonal
+ * Frobenius norm of every matrix is at most 1e-15 of its Frobenius norm.
+ * on_device = 1: A, lambda_out and vectors_out are device pointers, ordered
+ * on cuda_stream (NULL = the legacy default stream); 0: host pointers.  The
+ * call allocates its workspace (about 3 batch n^2 doubles) per call, blocks
+ * until done, and leaves A unchanged.  Errors: SWKB_ERR_INVALID_ARG (NULL,
+ * batch < 1, n < 1 or n > 8192, non-finite entries: no convergence),
+ * SWKB_ERR_OOM, SWKB_ERR_CUDA.
+ */
+swkb_status swkb_sym_eig(int32_t batch, int32_t n, const double* A, double* lambda_out,
+                         double* vectors_out, int32_t* sweeps_out, int32_t on_device,
+                         void* cuda_stream);
+
+typedef struct {
+  int32_t bc;      /* SWKB_BC_NEUMANN / SWKB_BC_DIRICHLET: grounded at z_a, field
+                      on z_a + m (z_b - z_a) / n_z, the period that of the S-WKB
+                      mirror, [2 z_a - z_b, z_b), z_c = z_a, one parity (cosines
+                      / sines); SWKB_BC_PERIODIC: period [z_a, z_b), field on
+                      z_a + m (z_b - z_a) / n_z, eps even about z_sym, both
+                      parities                                                */
+  double z_a, z_b;
+  double z_sym;    /* SWKB_BC_PERIODIC only: the symmetry point z_c, a grid
+                      point of the field                                      */
+  int32_t n_z;     /* field points                                             */
+  int32_t K;       /* modes kept: 1 <= K < N_period / 2                        */
+  int32_t n_q;     /* eps samples: n_q + 1 values at z_c + i L / (2 n_q),
+                      i = 0..n_q (the half period from z_c); n_q >= 2 K       */
+} swkb_hill_desc;
+
+/*
+ * The separation-of-variables field of `batch` problems sharing one
+ * swkb_hill_desc, each with its own wavenumber k[b] (host array) and
+ * permittivity eps[b][n_q + 1]: u0[b] (n_z complex128, the field at x = 0)
+ * -> u_out[b][r] (n_z complex128) at every range x[r], r < n_x (host array,
+ * x >= 0).  The projections are period means over the field points (exact for
+ * fields band-limited to |n| <= K; grounded fields are mirrored onto the
+ * period with zero at its top point).  lambda_out (NULL: not returned):
+ * batch x n_eig eigenvalues alpha_i^2, cosine block (K + 1) first, then sine
+ * block (K), each in no particular order; n_eig = K + 1 (Neumann), K
+ * (Dirichlet), 2 K + 1 (periodic).  on_device = 1: eps, u0, u_out and
+ * lambda_out are device pointers, ordered on cuda_stream; 0: host.
+ * Allocates its workspace per call and blocks until done.  Errors:
+ * SWKB_ERR_INVALID_ARG (NULL, sizes, K or n_q out of range, z_sym off the
+ * grid, k <= 0, x < 0, non-finite eps), SWKB_ERR_OOM, SWKB_ERR_CUDA.
+ */
+swkb_status swkb_hill_propagate(const swkb_hill_desc* desc, int32_t batch, const double* k,
+                                const double* eps, const double* u0, int32_t n_x,
+                                const double* x, double* u_out, double* lambda_out,
+                                int32_t on_device, void* cuda_stream);
+
 const char* swkb_last_error(void);
 const char* swkb_status_string(swkb_status s);
 

@@ -38,7 +38,8 @@ EXPORTED = ("swkb_options_default", "swkb_plan_create", "swkb_plan_get_info", "s
             "swkb_propagate_planes", "swkb_debug_screen", "swkb_plan_destroy", "swkb_plan_set_timing",
             "swkb_plan_get_stats", "swkb_server_create", "swkb_submit",
             "swkb_poll", "swkb_cancel", "swkb_server_get_stats", "swkb_server_destroy",
-            "swkb_last_error", "swkb_status_string", "swkb_modes_noalloc")
+            "swkb_last_error", "swkb_status_string", "swkb_modes_noalloc", "swkb_sym_eig",
+            "swkb_hill_propagate")
 
 
 class SwkbError(RuntimeError):
@@ -72,6 +73,11 @@ class swkb_plan_info(ctypes.Structure):
                 ("resum_points", c_int32), ("fft_n1", c_int32), ("dz", c_double),
                 ("period", c_double), ("eps_ref", c_double), ("device_bytes", c_size_t),
                 ("medium_pieces", c_int32), ("ctas_per_sm", c_int32)]
+
+
+class swkb_hill_desc(ctypes.Structure):
+    _fields_ = [("bc", c_int32), ("z_a", c_double), ("z_b", c_double), ("z_sym", c_double),
+                ("n_z", c_int32), ("K", c_int32), ("n_q", c_int32)]
 
 
 class swkb_plan_stats(ctypes.Structure):
@@ -131,6 +137,13 @@ def lib():
         L.swkb_server_destroy.restype = None
         L.swkb_modes_noalloc.argtypes = [c_void_p, c_int32, c_int32, c_void_p, c_void_p]
         L.swkb_modes_noalloc.restype = c_int32
+        L.swkb_sym_eig.argtypes = [c_int32, c_int32, c_void_p, c_void_p, c_void_p,
+                                   POINTER(c_int32), c_int32, c_void_p]
+        L.swkb_sym_eig.restype = c_int32
+        L.swkb_hill_propagate.argtypes = [POINTER(swkb_hill_desc), c_int32, c_void_p, c_void_p,
+                                          c_void_p, c_int32, c_void_p, c_void_p, c_void_p,
+                                          c_int32, c_void_p]
+        L.swkb_hill_propagate.restype = c_int32
         L.swkb_last_error.restype = c_char_p
         L.swkb_status_string.restype = c_char_p
         L.swkb_status_string.argtypes = [c_int32]
@@ -284,6 +297,80 @@ def swkb_modes_noalloc(u_ptr: int, n_fft: int, n_max: int, c_ptr: int, stream=No
     """Pruned DFT of a device field (device pointers) with no device allocation."""
     return lib().swkb_modes_noalloc(c_void_p(int(u_ptr)), int(n_fft), int(n_max),
                                     c_void_p(int(c_ptr)), stream)
+
+
+def swkb_sym_eig(A, vectors=True):
+    """Eigenpairs of real symmetric matrices (host arrays): A of shape
+    (n, n) or (batch, n, n).  Returns (lam, V, sweeps): lam[..., j] in no
+    particular order, row j of V[...] its unit eigenvector (None when
+    vectors is False)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    single = A.ndim == 2
+    if single:
+        A = A[None]
+    if A.ndim != 3 or A.shape[1] != A.shape[2]:
+        raise ValueError("A must be (n, n) or (batch, n, n)")
+    batch, n = A.shape[0], A.shape[1]
+    lam = np.empty((batch, n))
+    V = np.empty((batch, n, n)) if vectors else None
+    sweeps = c_int32(0)
+    check(lib().swkb_sym_eig(batch, n, A.ctypes.data_as(c_void_p), lam.ctypes.data_as(c_void_p),
+                             V.ctypes.data_as(c_void_p) if vectors else None, byref(sweeps), 0,
+                             None))
+    if single:
+        return lam[0], (V[0] if vectors else None), sweeps.value
+    return lam, V, sweeps.value
+
+
+def swkb_sym_eig_device(batch, n, a_ptr, lam_ptr, vec_ptr=None, stream=None) -> int:
+    """Device-pointer form; returns the sweeps used."""
+    sweeps = c_int32(0)
+    check(lib().swkb_sym_eig(int(batch), int(n), c_void_p(int(a_ptr)), c_void_p(int(lam_ptr)),
+                             c_void_p(int(vec_ptr)) if vec_ptr else None, byref(sweeps), 1,
+                             stream))
+    return sweeps.value
+
+
+def hill_desc(bc, z_a, z_b, n_z, K, n_q, z_sym=0.0) -> swkb_hill_desc:
+    return swkb_hill_desc(int(bc), float(z_a), float(z_b), float(z_sym), int(n_z), int(K),
+                          int(n_q))
+
+
+def hill_eigen_count(bc, K):
+    return {SWKB_BC_NEUMANN: K + 1, SWKB_BC_DIRICHLET: K}.get(bc, 2 * K + 1)
+
+
+def swkb_hill_propagate(desc: swkb_hill_desc, k, eps, u0, xs, eigenvalues=False):
+    """Separation-of-variables fields (host arrays): k (batch,), eps
+    (batch, n_q + 1), u0 (batch, n_z) complex, xs (n_x,) -> u (batch, n_x,
+    n_z) complex [, eigenvalues (batch, n_eig)]."""
+    k = np.ascontiguousarray(np.atleast_1d(k), dtype=np.float64)
+    batch = len(k)
+    eps = np.ascontiguousarray(eps, dtype=np.float64).reshape(batch, desc.n_q + 1)
+    u0 = np.ascontiguousarray(u0, dtype=np.complex128).reshape(batch, desc.n_z)
+    xs = np.ascontiguousarray(np.atleast_1d(xs), dtype=np.float64)
+    out = np.empty((batch, len(xs), desc.n_z), np.complex128)
+    lam = np.empty((batch, hill_eigen_count(desc.bc, desc.K))) if eigenvalues else None
+    check(lib().swkb_hill_propagate(byref(desc), batch, k.ctypes.data_as(c_void_p),
+                                    eps.ctypes.data_as(c_void_p), u0.ctypes.data_as(c_void_p),
+                                    len(xs), xs.ctypes.data_as(c_void_p),
+                                    out.ctypes.data_as(c_void_p),
+                                    lam.ctypes.data_as(c_void_p) if eigenvalues else None, 0,
+                                    None))
+    return (out, lam) if eigenvalues else out
+
+
+def swkb_hill_propagate_device(desc: swkb_hill_desc, k, eps_ptr, u0_ptr, xs, out_ptr,
+                               lam_ptr=None, stream=None) -> int:
+    """Device-pointer form (k and xs are host arrays)."""
+    k = np.ascontiguousarray(np.atleast_1d(k), dtype=np.float64)
+    xs = np.ascontiguousarray(np.atleast_1d(xs), dtype=np.float64)
+    return check(lib().swkb_hill_propagate(byref(desc), len(k), k.ctypes.data_as(c_void_p),
+                                           c_void_p(int(eps_ptr)), c_void_p(int(u0_ptr)),
+                                           len(xs), xs.ctypes.data_as(c_void_p),
+                                           c_void_p(int(out_ptr)),
+                                           c_void_p(int(lam_ptr)) if lam_ptr else None, 1,
+                                           stream))
 
 
 def swkb_last_error() -> str:

@@ -439,6 +439,51 @@ def batch_uneven(seed=4, n=64, **kw):
     return [random_request(rng, **kw) for _ in range(n)]
 
 
+class HillInputs:
+    """Inputs of one separation-of-variables problem batch: the boundary
+    condition and domain, K modes, eps sampled at n_q + 1 points of the half
+    period from the symmetry point z_c, wavenumbers, fields at x = 0 and the
+    output ranges."""
+
+    def __init__(self, name, bc, z_a, z_b, z_c, K, eps_half, k, u0, xs):
+        self.name, self.bc, self.z_a, self.z_b, self.z_c = name, bc, z_a, z_b, z_c
+        self.K = K
+        self.eps = np.atleast_2d(np.asarray(eps_half, float))
+        self.k = np.atleast_1d(np.asarray(k, float))
+        self.u0 = np.atleast_2d(np.asarray(u0, complex))
+        self.xs = np.atleast_1d(np.asarray(xs, float))
+        self.n_q = self.eps.shape[1] - 1
+        self.n_z = self.u0.shape[1]
+
+
+def hill_surface_duct_2km(K=640, n_q=1 << 15, batch=1):
+    """The 16384-point surface duct (200 m, Neumann ground, no absorber) as a
+    separation-of-variables problem at 2 km; batch > 1 adds ducts of seeds
+    3, 4, ... (own duct top and gradient) at the same wavenumber."""
+    epss, u0s, ks = [], [], []
+    for b in range(batch):
+        pb = config_surface_duct(seed=2 + b, n_screens=40, range_m=2000.0)
+        f = f_trilinear_duct(pb.meta["z_t"], pb.meta["g_d"])
+        s = (pb.z_b - pb.z_a) * np.arange(n_q + 1) / n_q
+        epss.append(f(s)[0])
+        u0s.append(pb.u0)
+        ks.append(pb.k)
+    return HillInputs(f"hill-surface-duct-16384-K{K}", BC_NEUMANN, pb.z_a, pb.z_b, pb.z_a, K,
+                      epss, ks, u0s, [2000.0])
+
+
+def hill_gaussian_duct_200km(n_q=4096, extra_modes=100):
+    """The 400 m periodic domain with the narrow Gaussian duct at its centre
+    (eps = 1 + 1e-4 exp(-1e-3 z^2), lambda = 5 cm, 0.2 deg beam), 200 km,
+    K = n_max + extra_modes, eps even about z_c = 0."""
+    pb = config_gaussian_duct_200km()
+    L = pb.z_b - pb.z_a
+    s = np.arange(n_q + 1) * L / (2 * n_q)
+    eps = f_gaussian(pb.meta["a"], pb.meta["b"])(s)[0]
+    return HillInputs("hill-gaussian-duct-200km", BC_PERIODIC, pb.z_a, pb.z_b, 0.0,
+                      pb.n_max + extra_modes, eps, pb.k, pb.u0, [200_000.0])
+
+
 WORKLOADS = {
     "unit-periodic-512": config_unit_periodic,
     "surface-duct-16384": config_surface_duct,

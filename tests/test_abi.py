@@ -48,7 +48,7 @@ def test_status_strings_and_defaults(built):
 
 
 STRUCTS = ("swkb_profile", "swkb_domain", "swkb_options", "swkb_plan_info", "swkb_plan_stats",
-           "swkb_request", "swkb_server_stats")
+           "swkb_request", "swkb_server_stats", "swkb_hill_desc")
 
 
 def test_struct_layouts_match_header(tmp_path):
