@@ -9,23 +9,28 @@
 //      padded to an even size P with zero rows);
 //   3. their eigenpairs by parallel cyclic Jacobi: each sweep runs the P - 1
 //      rounds of a round-robin tournament, a round rotating the P / 2
-//      disjoint index pairs (p, q) at once (one kernel computes the P / 2
-//      rotations, the next applies A <- J^T A J and W <- J^T W, a thread per
-//      2 x 2 block of A and per column pair of W); one sweep is one CUDA
-//      graph, replayed until the off-diagonal norm falls below 1e-15 of the
-//      Frobenius norm;
-//   4. the projections of the field on the basis (period means), on the
-//      eigenvectors (rows of W), the advance by exp(i alpha x) and the sum
-//      back onto the field points.
+//      disjoint index pairs (p, q) at once in one kernel (a thread per 2 x 2
+//      block of the upper triangle, folded so that no lane idles), which
+//      also makes the next round's rotations; one sweep is one CUDA graph,
+//      replayed until the off-diagonal norm falls below 1e-15 of the
+//      Frobenius norm.  The eigenvalues are the diagonal; the eigenvectors
+//      stay implicit: the field's basis projections are rotated along
+//      (a = W uh) and the rotations are logged, so that W^T is applied to the
+//      advanced coefficients by replaying the log backwards;
+//   4. the projections of the field on the basis (period means), the
+//      advance by exp(i alpha x) and the sum back onto the field points.
 //
-// A zero padding row never mixes with the others (its off-diagonal entries
-// stay exactly zero, so its rotations are the identity), and blocks (i, j)
-// and (j, i) are computed by the same arithmetic on the same operands, so A
-// stays exactly symmetric.
+// FP64 throughput is the scarce resource on this GPU (two FMAs per SM and
+// clock), so the rotation tangent is found in FP32 and only c, s and the
+// updates are FP64.  A zero padding row never mixes with the others (its
+// off-diagonal entries stay exactly zero, so its rotations are the
+// identity), and every block and its transpose are written from one
+// computation, so A stays exactly symmetric.
 
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -67,10 +72,6 @@ swkb_status hfail(swkb_status s, const char* fmt, ...) {
 constexpr int kMaxSweeps = 60;
 constexpr double kTol = 1e-15;
 constexpr int kThreads = 256;
-
-struct __align__(32) Rot {
-  double c, s, t, pad;
-};
 
 // round r (0 <= r < P - 1) of the circle tournament on P players: pair i
 __host__ __device__ inline void rr_pair(int r, int i, int P, int& p, int& q) {
@@ -171,7 +172,7 @@ __global__ void k_build(HillDims d, int n_mat, const double* k, const double* eh
       }
     }
     A[idx] = a;
-    W[idx] = r == c ? 1.0 : 0.0;
+    if (W) W[idx] = r == c ? 1.0 : 0.0;
   }
 }
 
@@ -189,7 +190,7 @@ __global__ void k_load_sym(const double* in, int n, int P, int n_mat, double* A,
       a = 0.5 * (m[(size_t)r * n + c] + m[(size_t)c * n + r]);
     }
     A[idx] = a;
-    W[idx] = r == c ? 1.0 : 0.0;
+    if (W) W[idx] = r == c ? 1.0 : 0.0;
   }
 }
 
@@ -197,10 +198,57 @@ __global__ void k_load_sym(const double* in, int n, int P, int n_mat, double* A,
 // Jacobi rounds
 // ---------------------------------------------------------------------------
 
-// the rotation annihilating A[p][q]: t = tan(theta), the root of t^2 + 2 t th
-// - 1 = 0 of smaller magnitude, th = (a_qq - a_pp) / (2 a_pq)
+// The rotation (c, s) of a pair: t = tan(theta) is the root of
+// t^2 + 2 t th - 1 = 0 of smaller magnitude, th = (a_qq - a_pp) / (2 a_pq),
+// found in FP32 (FP64 instructions are scarce here), then c = 1 / sqrt(1 +
+// t^2) and s = t c in FP64, so that J stays orthogonal to FP64 rounding: an
+// FP32 tangent leaves |a'_pq| ~ 1e-7 |a_pq|, which the following sweeps
+// remove like any other off-diagonal entry.  Operands FP32 cannot hold take
+// the FP64 formula.
+__device__ inline double2 rotation(double app, double aqq, double apq) {
+  if (apq == 0.0) return make_double2(1.0, 0.0);
+  const double d = aqq - app;
+  double t;
+  if (fabs(apq) > 1e-30 && fabs(apq) < 1e30 && fabs(d) < 1e30) {
+    const float th = (float)d / (2.0f * (float)apq);
+    const float ath = fabsf(th);
+    t = ath > 1e18f ? 0.5f / th : copysignf(1.0f, th) / (ath + sqrtf(1.0f + th * th));
+  } else {
+    const double th = d / (2.0 * apq);
+    const double ath = fabs(th);
+    t = ath > 1e150 ? 0.5 / th : copysign(1.0, th) / (ath + sqrt(1.0 + th * th));
+  }
+  const double c = rsqrt(1.0 + t * t);
+  return make_double2(c, t * c);
+}
+
+// player a in round r: its pair, whether it is the pair's p, and its partner
+__device__ inline int player_pair(int a, int r, int P, bool& is_p, int& partner) {
+  const int m = P - 1, npair = P / 2;
+  if (a == m) {
+    is_p = true;
+    partner = r;
+    return 0;
+  }
+  if (a == r) {
+    is_p = false;
+    partner = m;
+    return 0;
+  }
+  const int d = (a - r + m) % m;
+  if (d < npair) {
+    is_p = true;
+    partner = (r - d + m) % m;
+    return d;
+  }
+  is_p = false;
+  partner = (r + m - d) % m;
+  return m - d;
+}
+
+// rotations of one round from A (the first round of the first sweep)
 __global__ void k_rotations(const double* __restrict__ A, int P, int n_mat, int round,
-                            Rot* __restrict__ rot) {
+                            double2* __restrict__ rot) {
   const int npair = P / 2;
   const long long total = (long long)n_mat * npair;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
@@ -209,97 +257,213 @@ __global__ void k_rotations(const double* __restrict__ A, int P, int n_mat, int 
     int p, q;
     rr_pair(round, i, P, p, q);
     const double* a = A + (size_t)mat * P * P;
-    const double app = a[(size_t)p * P + p], aqq = a[(size_t)q * P + q];
-    const double apq = a[(size_t)p * P + q];
-    double t = 0.0;
-    if (apq != 0.0) {
-      const double th = (aqq - app) / (2.0 * apq);
-      const double ath = fabs(th);
-      t = ath > 1e150 ? 0.5 / th : copysign(1.0, th) / (ath + sqrt(1.0 + th * th));
-    }
-    const double c = 1.0 / sqrt(1.0 + t * t);
-    Rot o;
-    o.c = c;
-    o.s = t * c;
-    o.t = t;
-    o.pad = 0.0;
-    rot[idx] = o;
+    rot[idx] = rotation(a[(size_t)p * P + p], a[(size_t)q * P + q], a[(size_t)p * P + q]);
   }
 }
 
 // R = J_u^T B J_v with J = [[c, s], [-s, c]] on (p, q)
-__device__ inline void rotate_block(const Rot& ru, const Rot& rv, double b00, double b01,
-                                    double b10, double b11, double& r00, double& r01,
-                                    double& r10, double& r11) {
-  const double l00 = ru.c * b00 - ru.s * b10, l01 = ru.c * b01 - ru.s * b11;
-  const double l10 = ru.s * b00 + ru.c * b10, l11 = ru.s * b01 + ru.c * b11;
-  r00 = l00 * rv.c - l01 * rv.s;
-  r01 = l00 * rv.s + l01 * rv.c;
-  r10 = l10 * rv.c - l11 * rv.s;
-  r11 = l10 * rv.s + l11 * rv.c;
+__device__ inline void rotate_block(double cu, double su, double cv, double sv, double b00,
+                                    double b01, double b10, double b11, double& r00,
+                                    double& r01, double& r10, double& r11) {
+  const double l00 = cu * b00 - su * b10, l01 = cu * b01 - su * b11;
+  const double l10 = su * b00 + cu * b10, l11 = su * b01 + cu * b11;
+  r00 = l00 * cv - l01 * sv;
+  r01 = l00 * sv + l01 * cv;
+  r10 = l10 * cv - l11 * sv;
+  r11 = l10 * sv + l11 * cv;
 }
 
-// one round: A <- J^T A J (a thread per 2 x 2 block), W <- J^T W (a thread
-// per column and pair)
-__global__ void k_apply(double* __restrict__ A, double* __restrict__ W, int P, int n_mat,
-                        int round, const Rot* __restrict__ rot) {
+// One round: A <- J^T A J, a thread per 2 x 2 block (i <= j, which also
+// writes the transposed block (j, i); the upper triangle of blocks is folded
+// into a rectangle so no lane idles); with WITH_W, W <- J^T W, a thread per
+// column and pair; with vec, v <- J^T v for one complex vector per matrix, a
+// thread per pair.  The rotations of the next round are made here too:
+// their operands a_pp, a_qq, a_pq are written by three threads of this
+// round, each of which, after its writes and a fence, counts itself in on
+// the pair's counter; the third computes the rotation (reading the operands
+// from L2) and resets the counter.  No thread waits on another.
+template <bool WITH_W>
+__global__ void k_round(double* __restrict__ A, double* __restrict__ W,
+                        double2* __restrict__ vec, int P, int n_mat, int round,
+                        const double2* __restrict__ rot, double2* __restrict__ rot_next,
+                        unsigned* __restrict__ cnt) {
   const int npair = P / 2;
-  const long long nb = (long long)npair * npair, nw = (long long)npair * P;
-  const long long per = nb + nw, total = per * n_mat;
+  const int next = round + 1 == P - 1 ? 0 : round + 1;
+  const long long nb = (long long)((npair + 1) / 2) * (npair + 1);
+  const long long nw = WITH_W ? (long long)npair * P : 0;
+  const long long nv = vec ? npair : 0;
+  const long long per = nb + nw + nv, total = per * n_mat;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
     const int mat = (int)(idx / per);
     long long rem = idx - (long long)mat * per;
     double* a = A + (size_t)mat * P * P;
-    const Rot* rm = rot + (size_t)mat * npair;
+    const double2* rm = rot + (size_t)mat * npair;
     if (rem < nb) {
-      const int i = (int)(rem / npair), j = (int)(rem - (long long)i * npair);
+      const int rr = (int)(rem / (npair + 1)), cc = (int)(rem - (long long)rr * (npair + 1));
+      int i, j;
+      if (cc < npair - rr) {
+        i = rr;
+        j = rr + cc;
+      } else {
+        i = npair - 1 - rr;
+        if (i == rr) continue;   // the middle row of an odd count is done once
+        j = i + (cc - (npair - rr));
+      }
       int pi, qi, pj, qj;
       rr_pair(round, i, P, pi, qi);
       rr_pair(round, j, P, pj, qj);
+      const double2 ri = rm[i], rj = rm[j];
       double* e00 = a + (size_t)pi * P + pj;
       double* e01 = a + (size_t)pi * P + qj;
       double* e10 = a + (size_t)qi * P + pj;
       double* e11 = a + (size_t)qi * P + qj;
+      int ea[8], eb[8], ne;
       if (i == j) {
-        const Rot r = rm[i];
-        const double apq = *e01;
-        *e00 = *e00 - r.t * apq;
-        *e11 = *e11 + r.t * apq;
-        *e01 = 0.0;
-        *e10 = 0.0;
+        // the pair's own block in a form without cancellation at the scale
+        // of a_pp (exact for any rotation, not only the annihilating one):
+        // delta = s (2 c a_pq - s d), d = a_qq - a_pp; a'_pp = a_pp - delta,
+        // a'_qq = a_qq + delta, a'_pq = (c - s)(c + s) a_pq - c s d
+        const double c = ri.x, sn = ri.y;
+        const double app = *e00, aqq = *e11, apq = *e01, d = aqq - app;
+        const double delta = sn * (2.0 * c * apq - sn * d);
+        const double off = (c - sn) * (c + sn) * apq - c * sn * d;
+        *e00 = app - delta;
+        *e11 = aqq + delta;
+        *e01 = off;
+        *e10 = off;
+        ea[0] = pi; eb[0] = pi;
+        ea[1] = qi; eb[1] = qi;
+        ea[2] = pi; eb[2] = qi;
+        ea[3] = qi; eb[3] = pi;
+        ne = 4;
       } else {
-        const Rot ri = rm[i], rj = rm[j];
-        const double b00 = *e00, b01 = *e01, b10 = *e10, b11 = *e11;
         double r00, r01, r10, r11;
-        if (i < j) {
-          rotate_block(ri, rj, b00, b01, b10, b11, r00, r01, r10, r11);
-        } else {
-          // the transpose of block (j, i), computed exactly as its own thread does
-          double s00, s01, s10, s11;
-          rotate_block(rj, ri, b00, b10, b01, b11, s00, s01, s10, s11);
-          r00 = s00;
-          r01 = s10;
-          r10 = s01;
-          r11 = s11;
-        }
+        rotate_block(ri.x, ri.y, rj.x, rj.y, *e00, *e01, *e10, *e11, r00, r01, r10, r11);
         *e00 = r00;
         *e01 = r01;
         *e10 = r10;
         *e11 = r11;
+        a[(size_t)pj * P + pi] = r00;
+        a[(size_t)qj * P + pi] = r01;
+        a[(size_t)pj * P + qi] = r10;
+        a[(size_t)qj * P + qi] = r11;
+        ea[0] = pi; eb[0] = pj;
+        ea[1] = pi; eb[1] = qj;
+        ea[2] = qi; eb[2] = pj;
+        ea[3] = qi; eb[3] = qj;
+        ea[4] = pj; eb[4] = pi;
+        ea[5] = qj; eb[5] = pi;
+        ea[6] = pj; eb[6] = qi;
+        ea[7] = qj; eb[7] = qi;
+        ne = 8;
       }
-    } else {
+      // the next round's operands among the entries written here: at most
+      // two, as each of the thread's two rows has one partner next round
+      int key0 = -1, key1 = -1;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        if (e >= ne) break;
+        bool is_p;
+        int partner;
+        const int k = player_pair(ea[e], next, P, is_p, partner);
+        if (ea[e] == eb[e] || (is_p && partner == eb[e])) {
+          if (key0 < 0) key0 = k;
+          else key1 = k;
+        }
+      }
+      if (key0 < 0) continue;
+      __threadfence();
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int key = e == 0 ? key0 : key1;
+        if (key < 0) break;
+        unsigned* c = cnt + (size_t)mat * npair + key;
+        if (atomicAdd(c, 1u) == 2u) {
+          __threadfence();
+          int p, q;
+          rr_pair(next, key, P, p, q);
+          rot_next[(size_t)mat * npair + key] =
+              rotation(__ldcg(a + (size_t)p * P + p), __ldcg(a + (size_t)q * P + q),
+                       __ldcg(a + (size_t)p * P + q));
+          *c = 0u;
+        }
+      }
+    } else if (WITH_W && rem < nb + nw) {
       rem -= nb;
       const int i = (int)(rem / P), col = (int)(rem - (long long)i * P);
       int p, q;
       rr_pair(round, i, P, p, q);
       double* w = W + (size_t)mat * P * P;
-      const Rot r = rm[i];
+      const double2 r = rm[i];
       const double wp = w[(size_t)p * P + col], wq = w[(size_t)q * P + col];
-      w[(size_t)p * P + col] = r.c * wp - r.s * wq;
-      w[(size_t)q * P + col] = r.s * wp + r.c * wq;
+      w[(size_t)p * P + col] = r.x * wp - r.y * wq;
+      w[(size_t)q * P + col] = r.y * wp + r.x * wq;
+    } else {
+      const int i = (int)(rem - nb - nw);
+      int p, q;
+      rr_pair(round, i, P, p, q);
+      double2* v = vec + (size_t)mat * P;
+      const double2 r = rm[i];
+      const double2 vp = v[p], vq = v[q];
+      v[p] = make_double2(r.x * vp.x - r.y * vq.x, r.x * vp.y - r.y * vq.y);
+      v[q] = make_double2(r.y * vp.x + r.x * vq.x, r.y * vp.y + r.x * vq.y);
     }
   }
+}
+
+// Replays logged rotations on complex vectors, one CTA per vector held in
+// shared memory: FORWARD applies v <- J^T v round by round (v <- W v), the
+// reverse applies v <- J v from the last round back (v <- W^T v).  Each
+// thread fetches its next round's rotations before the current round's
+// barrier.
+constexpr int kReplayMaxPerThread = 4;
+
+template <bool FORWARD>
+__global__ void k_replay(const double2* __restrict__ log, int n_rounds, int P, int n_mat,
+                         int vecs_per_mat, double2* __restrict__ vecs) {
+  extern __shared__ double2 v[];
+  const int npair = P / 2;
+  const int vec = blockIdx.x, mat = vec / vecs_per_mat;
+  double2* gv = vecs + (size_t)vec * P;
+  for (int i = threadIdx.x; i < P; i += blockDim.x) v[i] = gv[i];
+  auto rot_at = [&](int step, int i) {
+    const int g = FORWARD ? step : n_rounds - 1 - step;
+    return log[((size_t)g * n_mat + mat) * npair + i];
+  };
+  double2 cur[kReplayMaxPerThread];
+  for (int k = 0; k < kReplayMaxPerThread; ++k) {
+    const int i = threadIdx.x + k * blockDim.x;
+    if (i < npair && n_rounds > 0) cur[k] = rot_at(0, i);
+  }
+  __syncthreads();
+  for (int step = 0; step < n_rounds; ++step) {
+    const int g = FORWARD ? step : n_rounds - 1 - step;
+    const int r = g % (P - 1);
+    double2 nxt[kReplayMaxPerThread];
+    for (int k = 0; k < kReplayMaxPerThread; ++k) {
+      const int i = threadIdx.x + k * blockDim.x;
+      if (i < npair && step + 1 < n_rounds) nxt[k] = rot_at(step + 1, i);
+    }
+    for (int k = 0; k < kReplayMaxPerThread; ++k) {
+      const int i = threadIdx.x + k * blockDim.x;
+      if (i >= npair) break;
+      int p, q;
+      rr_pair(r, i, P, p, q);
+      const double c = cur[k].x, s = cur[k].y;
+      const double2 vp = v[p], vq = v[q];
+      if (FORWARD) {
+        v[p] = make_double2(c * vp.x - s * vq.x, c * vp.y - s * vq.y);
+        v[q] = make_double2(s * vp.x + c * vq.x, s * vp.y + c * vq.y);
+      } else {
+        v[p] = make_double2(c * vp.x + s * vq.x, c * vp.y + s * vq.y);
+        v[q] = make_double2(c * vq.x - s * vp.x, c * vq.y - s * vp.y);
+      }
+    }
+    for (int k = 0; k < kReplayMaxPerThread; ++k) cur[k] = nxt[k];
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < P; i += blockDim.x) gv[i] = v[i];
 }
 
 // norms[mat] = (sum of squared off-diagonal entries, sum of all squares)
@@ -374,29 +538,6 @@ __global__ void k_project(const double2* u0, FieldDims f, HillDims d, const doub
   }
 }
 
-// a[mat][j] = sum_n W[j][n] uh[n]; a warp per (j, mat)
-__global__ void k_eigen_coefficients(const double* W, const double2* uh, int P, int n_mat,
-                                     double2* coef) {
-  const int lane = threadIdx.x & 31;
-  const long long n_warps = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-       warp < (long long)n_mat * P; warp += n_warps) {
-    const int mat = (int)(warp / P), j = (int)(warp - (long long)mat * P);
-    const double* w = W + ((size_t)mat * P + j) * P;
-    const double2* u = uh + (size_t)mat * P;
-    double sr = 0.0, si = 0.0;
-    for (int n = lane; n < P; n += 32) {
-      sr += w[n] * u[n].x;
-      si += w[n] * u[n].y;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      sr += __shfl_xor_sync(0xffffffffu, sr, o);
-      si += __shfl_xor_sync(0xffffffffu, si, o);
-    }
-    if (lane == 0) coef[warp] = make_double2(sr, si);
-  }
-}
-
 // ph[mat][r][j] = a_j exp(i alpha_j x_r), alpha_j = sqrt(lambda_j) (principal)
 __global__ void k_advance_coefficients(const double* A, const double2* coef, HillDims d,
                                        int n_mat, const double* xs, int n_x, double2* ph) {
@@ -425,27 +566,6 @@ __global__ void k_advance_coefficients(const double* A, const double2* coef, Hil
       out = make_double2(a.x * er - a.y * ei, a.x * ei + a.y * er);
     }
     ph[idx] = out;
-  }
-}
-
-// g[mat][r][n] = sum_j W[j][n] ph[mat][r][j]
-__global__ void k_eigen_sum(const double* W, const double2* ph, int P, int n_mat, int n_x,
-                            double2* g) {
-  const long long total = (long long)n_mat * n_x * P;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int n = (int)(idx % P);
-    const long long mr = idx / P;
-    const int mat = (int)(mr / n_x);
-    const double* w = W + (size_t)mat * P * P + n;
-    const double2* p = ph + mr * P;
-    double sr = 0.0, si = 0.0;
-    for (int j = 0; j < P; ++j) {
-      const double wj = w[(size_t)j * P];
-      sr += wj * p[j].x;
-      si += wj * p[j].y;
-    }
-    g[idx] = make_double2(sr, si);
   }
 }
 
@@ -537,23 +657,47 @@ struct Scratch {
   }
 };
 
-// Jacobi sweeps on A (n_mat matrices of P x P) until converged; the sweep
-// (P - 1 rounds and the norms) is captured once as a graph
-swkb_status jacobi(Scratch& s, double* A, double* W, int P, int n_mat, int* sweeps_out) {
+// Rotations of every round of every sweep, in order, (c, s) per pair:
+// log[(round * n_mat + mat) * P / 2 + pair]
+struct RotLog {
+  double2* d = nullptr;
+  int rounds = 0;
+};
+
+// Jacobi sweeps on A (n_mat matrices of P x P; W and vec, one complex
+// vector per matrix, rotated along when not NULL) until converged.  A sweep (P - 1 fused rounds and the norms) is captured once as
+// a graph; rotations live in P slots of a round each: round r reads slot r
+// and makes the next round's in slot r + 1, the last round the next sweep's
+// first in slot P - 1, which the sweep's first node copies to slot 0.  With
+// log, slots 0..P-2 are appended to it after every sweep.
+swkb_status jacobi(Scratch& s, double* A, double* W, double2* vec, int P, int n_mat,
+                   int* sweeps_out, RotLog* log) {
   const int npair = P / 2;
-  Rot* rot = nullptr;
+  const size_t per_round = (size_t)n_mat * npair;
+  double2* slots = nullptr;
+  unsigned* cnt = nullptr;
   double* norms = nullptr;
-  HTRY(s.alloc(&rot, (size_t)n_mat * npair));
+  HTRY(s.alloc(&slots, (size_t)P * per_round));
+  HTRY(s.alloc(&cnt, per_round));
   HTRY(s.alloc(&norms, 2 * (size_t)n_mat));
   HCK(cudaMallocHost(&s.host_norms, 2 * sizeof(double) * n_mat));
-  const long long apply_work = (long long)n_mat * ((long long)npair * npair + (long long)npair * P);
-  const int g_rot = grid_for((long long)n_mat * npair), g_app = grid_for(apply_work);
+  HCK(cudaMemsetAsync(cnt, 0, per_round * sizeof(unsigned), s.stream));
+  const long long work = (long long)n_mat * ((long long)((npair + 1) / 2) * (npair + 1) +
+                                             (W ? (long long)npair * P : 0) + (vec ? npair : 0));
+  const int g_round = grid_for(work);
   const int norm_cols = std::max(1, std::min(64, (int)(((long long)P * P + 4095) / 4096)));
+  double2* last = slots + (size_t)(P - 1) * per_round;
   cudaGraph_t graph = nullptr;
   HCK(cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal));
+  cudaMemcpyAsync(slots, last, per_round * sizeof(double2), cudaMemcpyDeviceToDevice, s.stream);
   for (int r = 0; r < P - 1; ++r) {
-    k_rotations<<<g_rot, kThreads, 0, s.stream>>>(A, P, n_mat, r, rot);
-    k_apply<<<g_app, kThreads, 0, s.stream>>>(A, W, P, n_mat, r, rot);
+    const double2* cur = slots + (size_t)r * per_round;
+    double2* nxt = slots + (size_t)(r + 1) * per_round;   // slot P - 1 after the last round
+    if (W)
+      k_round<true><<<g_round, kThreads, 0, s.stream>>>(A, W, vec, P, n_mat, r, cur, nxt, cnt);
+    else
+      k_round<false><<<g_round, kThreads, 0, s.stream>>>(A, nullptr, vec, P, n_mat, r, cur, nxt,
+                                                          cnt);
   }
   cudaMemsetAsync(norms, 0, 2 * sizeof(double) * n_mat, s.stream);
   k_norms<<<dim3(norm_cols, n_mat), kThreads, 0, s.stream>>>(A, P, norms);
@@ -567,9 +711,11 @@ swkb_status jacobi(Scratch& s, double* A, double* W, int P, int n_mat, int* swee
   const cudaError_t ei = cudaGraphInstantiate(&s.sweep, graph, 0);
   cudaGraphDestroy(graph);
   if (ei != cudaSuccess) return hfail(SWKB_ERR_CUDA, "sweep graph: %s", cudaGetErrorString(ei));
-  // the Frobenius norms are invariant under the rotations: take them before
+  // the Frobenius norms are invariant under the rotations: take them before;
+  // the first round's rotations go to slot P - 1
   HCK(cudaMemsetAsync(norms, 0, 2 * sizeof(double) * n_mat, s.stream));
   k_norms<<<dim3(norm_cols, n_mat), kThreads, 0, s.stream>>>(A, P, norms);
+  k_rotations<<<grid_for((long long)per_round), kThreads, 0, s.stream>>>(A, P, n_mat, 0, last);
   HCK(cudaGetLastError());
   HCK(cudaMemcpyAsync(s.host_norms, norms, 2 * sizeof(double) * n_mat, cudaMemcpyDeviceToHost,
                       s.stream));
@@ -580,6 +726,9 @@ swkb_status jacobi(Scratch& s, double* A, double* W, int P, int n_mat, int* swee
     if (!std::isfinite(fro[m]))
       return hfail(SWKB_ERR_INVALID_ARG, "matrix %d has non-finite entries", m);
   }
+  const size_t sweep_log = (size_t)(P - 1) * per_round;
+  double2* logbuf = nullptr;
+  int log_cap = 0;
   int sweeps = 0;
   bool done = true;
   for (int m = 0; m < n_mat; ++m) done = done && s.host_norms[2 * m] <= kTol * kTol * fro[m];
@@ -588,6 +737,20 @@ swkb_status jacobi(Scratch& s, double* A, double* W, int P, int n_mat, int* swee
       return hfail(SWKB_ERR_INVALID_ARG, "Jacobi iteration did not converge in %d sweeps",
                    kMaxSweeps);
     HCK(cudaGraphLaunch(s.sweep, s.stream));
+    if (log) {
+      if (sweeps == log_cap) {   // room for twice as many sweeps (8 at first)
+        const int cap = std::max(8, 2 * log_cap);
+        double2* grown = nullptr;
+        HTRY(s.alloc(&grown, (size_t)cap * sweep_log));
+        if (logbuf)
+          HCK(cudaMemcpyAsync(grown, logbuf, (size_t)sweeps * sweep_log * sizeof(double2),
+                              cudaMemcpyDeviceToDevice, s.stream));
+        logbuf = grown;
+        log_cap = cap;
+      }
+      HCK(cudaMemcpyAsync(logbuf + (size_t)sweeps * sweep_log, slots,
+                          sweep_log * sizeof(double2), cudaMemcpyDeviceToDevice, s.stream));
+    }
     HCK(cudaStreamSynchronize(s.stream));
     ++sweeps;
     done = true;
@@ -599,6 +762,28 @@ swkb_status jacobi(Scratch& s, double* A, double* W, int P, int n_mat, int* swee
     }
   }
   if (sweeps_out) *sweeps_out = sweeps;
+  if (log) {
+    log->d = logbuf;
+    log->rounds = sweeps * (P - 1);
+  }
+  return SWKB_OK;
+}
+
+// v <- W v (forward) or W^T v for n_vec vectors of P complex values
+template <bool FORWARD>
+swkb_status replay(Scratch& s, const RotLog& log, int P, int n_mat, int vecs_per_mat,
+                   double2* vecs) {
+  const int npair = P / 2;
+  const int threads = std::min(1024, std::max(32, (npair + 31) / 32 * 32));
+  if ((npair + threads - 1) / threads > kReplayMaxPerThread)
+    return hfail(SWKB_ERR_INVALID_ARG, "matrix too large for the rotation replay");
+  const size_t smem = (size_t)P * sizeof(double2);
+  if (smem > 48 * 1024)
+    HCK(cudaFuncSetAttribute(k_replay<FORWARD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem));
+  k_replay<FORWARD><<<n_mat * vecs_per_mat, threads, smem, s.stream>>>(log.d, log.rounds, P,
+                                                                       n_mat, vecs_per_mat, vecs);
+  HCK(cudaGetLastError());
   return SWKB_OK;
 }
 
@@ -621,7 +806,7 @@ swkb_status sym_eig(int batch, int n, const double* A_in, double* lam_out, doubl
   const size_t nn = (size_t)n * n * batch, PP = (size_t)P * P * batch;
   double *A = nullptr, *W = nullptr, *src = nullptr, *lam = nullptr, *vec = nullptr;
   HTRY(s.alloc(&A, PP));
-  HTRY(s.alloc(&W, PP));
+  if (vec_out) HTRY(s.alloc(&W, PP));   // eigenvectors accumulated only when wanted
   if (on_device) {
     src = (double*)A_in;
     lam = lam_out;
@@ -634,7 +819,7 @@ swkb_status sym_eig(int batch, int n, const double* A_in, double* lam_out, doubl
   }
   k_load_sym<<<grid_for((long long)PP), kThreads, 0, s.stream>>>(src, n, P, batch, A, W);
   HCK(cudaGetLastError());
-  HTRY(jacobi(s, A, W, P, batch, sweeps_out));
+  HTRY(jacobi(s, A, W, nullptr, P, batch, sweeps_out, nullptr));
   k_copy_leading<<<grid_for((long long)nn), kThreads, 0, s.stream>>>(A, W, n, P, batch, lam, vec);
   HCK(cudaGetLastError());
   if (!on_device) {
@@ -690,17 +875,16 @@ swkb_status hill_propagate(const swkb_hill_desc* d, int batch, const double* k,
   hd.kappa1 = 2.0 * M_PI / L;
   const int n_mat = batch * hd.n_par, P = hd.P, J = 2 * d->K + 1;
   const int n_eig = hd.n_par == 2 ? 2 * d->K + 1 : (hd.par0 ? d->K : d->K + 1);
-  if ((double)P * P * n_mat * 2 * sizeof(double) > 64e9)
-    return hfail(SWKB_ERR_INVALID_ARG, "batch x K too large for one call");
+  if (P > 8192 || (double)P * P * n_mat * sizeof(double) > 64e9)
+    return hfail(SWKB_ERR_INVALID_ARG, "K or batch x K too large for one call");
 
   Scratch s;
   HTRY(open_stream(s, on_device, user_stream));
   const size_t n_eps = (size_t)batch * (d->n_q + 1), n_u = (size_t)batch * d->n_z;
   const size_t n_out = (size_t)batch * n_x * d->n_z;
   double *eps = nullptr, *kd = nullptr, *xd = nullptr, *tq = nullptr, *eh = nullptr;
-  double *A = nullptr, *W = nullptr, *lam = nullptr;
-  double2 *u0 = nullptr, *tab = nullptr, *uh = nullptr, *coef = nullptr, *ph = nullptr;
-  double2 *g = nullptr, *out = nullptr;
+  double *A = nullptr, *lam = nullptr;
+  double2 *u0 = nullptr, *tab = nullptr, *uh = nullptr, *ph = nullptr, *out = nullptr;
   if (on_device) {
     eps = (double*)eps_in;
     u0 = (double2*)u0_in;
@@ -720,28 +904,27 @@ swkb_status hill_propagate(const swkb_hill_desc* d, int batch, const double* k,
   HTRY(s.alloc(&tab, f.N));
   HTRY(s.alloc(&eh, (size_t)batch * J));
   HTRY(s.alloc(&A, (size_t)n_mat * P * P));
-  HTRY(s.alloc(&W, (size_t)n_mat * P * P));
   HTRY(s.alloc(&uh, (size_t)n_mat * P));
-  HTRY(s.alloc(&coef, (size_t)n_mat * P));
   HTRY(s.alloc(&ph, (size_t)n_mat * n_x * P));
-  HTRY(s.alloc(&g, (size_t)n_mat * n_x * P));
   HCK(cudaMemcpyAsync(kd, k, batch * sizeof(double), cudaMemcpyHostToDevice, s.stream));
   HCK(cudaMemcpyAsync(xd, x, n_x * sizeof(double), cudaMemcpyHostToDevice, s.stream));
 
   k_dct_table<<<grid_for(2LL * d->n_q), kThreads, 0, s.stream>>>(tq, d->n_q);
   k_period_table<<<grid_for(f.N), kThreads, 0, s.stream>>>(tab, f.N);
   k_eps_means<<<dim3(J, batch), kThreads, 0, s.stream>>>(eps, d->n_q, tq, J, eh);
-  k_build<<<grid_for((long long)n_mat * P * P), kThreads, 0, s.stream>>>(hd, n_mat, kd, eh, A, W);
+  k_build<<<grid_for((long long)n_mat * P * P), kThreads, 0, s.stream>>>(hd, n_mat, kd, eh, A,
+                                                                         nullptr);
   HCK(cudaGetLastError());
-  HTRY(jacobi(s, A, W, P, n_mat, nullptr));
+  // eigenvalues on the diagonal of A; the eigenvectors stay implicit, as the
+  // logged rotations W = J_T^T ... J_1^T
+  // the field's basis projections uh ride along the rotations: a = W uh
   k_project<<<dim3(P, n_mat), kThreads, 0, s.stream>>>(u0, f, hd, tab, uh);
-  k_eigen_coefficients<<<grid_for((long long)n_mat * P * 32), kThreads, 0, s.stream>>>(
-      W, uh, P, n_mat, coef);
+  RotLog lg;
+  HTRY(jacobi(s, A, nullptr, uh, P, n_mat, nullptr, &lg));
   k_advance_coefficients<<<grid_for((long long)n_mat * n_x * P), kThreads, 0, s.stream>>>(
-      A, coef, hd, n_mat, xd, n_x, ph);
-  k_eigen_sum<<<grid_for((long long)n_mat * n_x * P), kThreads, 0, s.stream>>>(W, ph, P, n_mat,
-                                                                                n_x, g);
-  k_synthesize<<<grid_for((long long)n_out), kThreads, 0, s.stream>>>(g, f, hd, batch, n_x, tab,
+      A, uh, hd, n_mat, xd, n_x, ph);                     // a_j exp(i alpha_j x)
+  HTRY(replay<false>(s, lg, P, n_mat, n_x, ph));          // g = W^T (a exp(i alpha x))
+  k_synthesize<<<grid_for((long long)n_out), kThreads, 0, s.stream>>>(ph, f, hd, batch, n_x, tab,
                                                                        out);
   if (lam) k_eigenvalues<<<grid_for((long long)batch * n_eig), kThreads, 0, s.stream>>>(
       A, hd, batch, lam);
