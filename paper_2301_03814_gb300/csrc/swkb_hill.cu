@@ -72,16 +72,23 @@ swkb_status hfail(swkb_status s, const char* fmt, ...) {
 constexpr int kMaxSweeps = 60;
 constexpr double kTol = 1e-15;
 constexpr int kThreads = 256;
+// Jacobi rounds use small CTAs: a round has only P^2 / 8 blocks of work, and
+// spreading them evenly over the SMs matters more than CTA size
+constexpr int kRoundThreads = 64;
 
 // round r (0 <= r < P - 1) of the circle tournament on P players: pair i
+// is (P - 1, r) for i = 0 and ((r + i) mod m, (r - i) mod m), m = P - 1,
+// otherwise (0 <= r, i < m, so one conditional add or subtract reduces)
 __host__ __device__ inline void rr_pair(int r, int i, int P, int& p, int& q) {
   const int m = P - 1;
   if (i == 0) {
     p = m;
     q = r;
   } else {
-    p = (r + i) % m;
-    q = (r - i + m) % m;
+    p = r + i;
+    if (p >= m) p -= m;
+    q = r - i;
+    if (q < 0) q += m;
   }
 }
 
@@ -223,6 +230,7 @@ __device__ inline double2 rotation(double app, double aqq, double apq) {
 }
 
 // player a in round r: its pair, whether it is the pair's p, and its partner
+// (the pairs i >= 1 of a round have p + q = 2 r mod m)
 __device__ inline int player_pair(int a, int r, int P, bool& is_p, int& partner) {
   const int m = P - 1, npair = P / 2;
   if (a == m) {
@@ -235,14 +243,17 @@ __device__ inline int player_pair(int a, int r, int P, bool& is_p, int& partner)
     partner = m;
     return 0;
   }
-  const int d = (a - r + m) % m;
+  int d = a - r;
+  if (d < 0) d += m;
   if (d < npair) {
     is_p = true;
-    partner = (r - d + m) % m;
+    partner = r - d;
+    if (partner < 0) partner += m;
     return d;
   }
   is_p = false;
-  partner = (r + m - d) % m;
+  partner = r + (m - d);
+  if (partner >= m) partner -= m;
   return m - d;
 }
 
@@ -282,19 +293,23 @@ __device__ inline void rotate_block(double cu, double su, double cv, double sv, 
 // round, each of which, after its writes and a fence, counts itself in on
 // the pair's counter; the third computes the rotation (reading the operands
 // from L2) and resets the counter.  No thread waits on another.
+//
+// Operands are read through L2 (ld.global.cg): they were written by other
+// CTAs, in this round's predecessor or, for the next rotations, in this one.
 template <bool WITH_W>
-__global__ void k_round(double* __restrict__ A, double* __restrict__ W,
-                        double2* __restrict__ vec, int P, int n_mat, int round,
-                        const double2* __restrict__ rot, double2* __restrict__ rot_next,
-                        unsigned* __restrict__ cnt) {
+__device__ __forceinline__ void round_items(double* __restrict__ A, double* __restrict__ W,
+                                            double2* __restrict__ vec, int P, int n_mat,
+                                            int round, const double2* __restrict__ rot,
+                                            double2* __restrict__ rot_next,
+                                            unsigned* __restrict__ cnt, long long first,
+                                            long long stride) {
   const int npair = P / 2;
   const int next = round + 1 == P - 1 ? 0 : round + 1;
   const long long nb = (long long)((npair + 1) / 2) * (npair + 1);
   const long long nw = WITH_W ? (long long)npair * P : 0;
   const long long nv = vec ? npair : 0;
   const long long per = nb + nw + nv, total = per * n_mat;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
+  for (long long idx = first; idx < total; idx += stride) {
     const int mat = (int)(idx / per);
     long long rem = idx - (long long)mat * per;
     double* a = A + (size_t)mat * P * P;
@@ -313,33 +328,28 @@ __global__ void k_round(double* __restrict__ A, double* __restrict__ W,
       int pi, qi, pj, qj;
       rr_pair(round, i, P, pi, qi);
       rr_pair(round, j, P, pj, qj);
-      const double2 ri = rm[i], rj = rm[j];
+      const double2 ri = __ldcg(rm + i), rj = __ldcg(rm + j);
       double* e00 = a + (size_t)pi * P + pj;
       double* e01 = a + (size_t)pi * P + qj;
       double* e10 = a + (size_t)qi * P + pj;
       double* e11 = a + (size_t)qi * P + qj;
-      int ea[8], eb[8], ne;
       if (i == j) {
         // the pair's own block in a form without cancellation at the scale
         // of a_pp (exact for any rotation, not only the annihilating one):
         // delta = s (2 c a_pq - s d), d = a_qq - a_pp; a'_pp = a_pp - delta,
         // a'_qq = a_qq + delta, a'_pq = (c - s)(c + s) a_pq - c s d
         const double c = ri.x, sn = ri.y;
-        const double app = *e00, aqq = *e11, apq = *e01, d = aqq - app;
+        const double app = __ldcg(e00), aqq = __ldcg(e11), apq = __ldcg(e01), d = aqq - app;
         const double delta = sn * (2.0 * c * apq - sn * d);
         const double off = (c - sn) * (c + sn) * apq - c * sn * d;
         *e00 = app - delta;
         *e11 = aqq + delta;
         *e01 = off;
         *e10 = off;
-        ea[0] = pi; eb[0] = pi;
-        ea[1] = qi; eb[1] = qi;
-        ea[2] = pi; eb[2] = qi;
-        ea[3] = qi; eb[3] = pi;
-        ne = 4;
       } else {
         double r00, r01, r10, r11;
-        rotate_block(ri.x, ri.y, rj.x, rj.y, *e00, *e01, *e10, *e11, r00, r01, r10, r11);
+        rotate_block(ri.x, ri.y, rj.x, rj.y, __ldcg(e00), __ldcg(e01), __ldcg(e10), __ldcg(e11),
+                     r00, r01, r10, r11);
         *e00 = r00;
         *e01 = r01;
         *e10 = r10;
@@ -348,35 +358,34 @@ __global__ void k_round(double* __restrict__ A, double* __restrict__ W,
         a[(size_t)qj * P + pi] = r01;
         a[(size_t)pj * P + qi] = r10;
         a[(size_t)qj * P + qi] = r11;
-        ea[0] = pi; eb[0] = pj;
-        ea[1] = pi; eb[1] = qj;
-        ea[2] = qi; eb[2] = pj;
-        ea[3] = qi; eb[3] = qj;
-        ea[4] = pj; eb[4] = pi;
-        ea[5] = qj; eb[5] = pi;
-        ea[6] = pj; eb[6] = qi;
-        ea[7] = qj; eb[7] = qi;
-        ne = 8;
       }
-      // the next round's operands among the entries written here: at most
-      // two, as each of the thread's two rows has one partner next round
-      int key0 = -1, key1 = -1;
-#pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        if (e >= ne) break;
-        bool is_p;
-        int partner;
-        const int k = player_pair(ea[e], next, P, is_p, partner);
-        if (ea[e] == eb[e] || (is_p && partner == eb[e])) {
-          if (key0 < 0) key0 = k;
-          else key1 = k;
+      // The next round's operands among the entries written here.  Rows pi
+      // and qi each have one partner next round; where it is a column of
+      // this block, the block holds that pair's a_pq (once: (p, q) and
+      // (q, p) are written together).  A diagonal block also holds a_pp of
+      // its two rows' pairs, and, for P = 2 only (one round per sweep), the
+      // same pair's a_pq.
+      bool is_p;
+      int tp, tq;
+      const int kp = player_pair(pi, next, P, is_p, tp);
+      const int kq = player_pair(qi, next, P, is_p, tq);
+      int key0 = -1, key1 = -1, key2 = -1;
+      if (i == j) {
+        key0 = kp;
+        key1 = kq;
+        if (tp == qi) key2 = kp;
+      } else {
+        if (tp == pj || tp == qj) key0 = kp;
+        if (tq == pj || tq == qj) {
+          if (key0 < 0) key0 = kq;
+          else key1 = kq;
         }
       }
       if (key0 < 0) continue;
       __threadfence();
 #pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const int key = e == 0 ? key0 : key1;
+      for (int e = 0; e < 3; ++e) {
+        const int key = e == 0 ? key0 : (e == 1 ? key1 : key2);
         if (key < 0) break;
         unsigned* c = cnt + (size_t)mat * npair + key;
         if (atomicAdd(c, 1u) == 2u) {
@@ -395,8 +404,8 @@ __global__ void k_round(double* __restrict__ A, double* __restrict__ W,
       int p, q;
       rr_pair(round, i, P, p, q);
       double* w = W + (size_t)mat * P * P;
-      const double2 r = rm[i];
-      const double wp = w[(size_t)p * P + col], wq = w[(size_t)q * P + col];
+      const double2 r = __ldcg(rm + i);
+      const double wp = __ldcg(w + (size_t)p * P + col), wq = __ldcg(w + (size_t)q * P + col);
       w[(size_t)p * P + col] = r.x * wp - r.y * wq;
       w[(size_t)q * P + col] = r.y * wp + r.x * wq;
     } else {
@@ -404,12 +413,23 @@ __global__ void k_round(double* __restrict__ A, double* __restrict__ W,
       int p, q;
       rr_pair(round, i, P, p, q);
       double2* v = vec + (size_t)mat * P;
-      const double2 r = rm[i];
-      const double2 vp = v[p], vq = v[q];
+      const double2 r = __ldcg(rm + i);
+      const double2 vp = __ldcg(v + p), vq = __ldcg(v + q);
       v[p] = make_double2(r.x * vp.x - r.y * vq.x, r.x * vp.y - r.y * vq.y);
       v[q] = make_double2(r.y * vp.x + r.x * vq.x, r.y * vp.y + r.x * vq.y);
     }
   }
+}
+
+// one round per launch
+template <bool WITH_W>
+__global__ void k_round(double* __restrict__ A, double* __restrict__ W,
+                        double2* __restrict__ vec, int P, int n_mat, int round,
+                        const double2* __restrict__ rot, double2* __restrict__ rot_next,
+                        unsigned* __restrict__ cnt) {
+  round_items<WITH_W>(A, W, vec, P, n_mat, round, rot, rot_next, cnt,
+                      blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                      (long long)gridDim.x * blockDim.x);
 }
 
 // Replays logged rotations on complex vectors, one CTA per vector held in
@@ -684,7 +704,7 @@ swkb_status jacobi(Scratch& s, double* A, double* W, double2* vec, int P, int n_
   HCK(cudaMemsetAsync(cnt, 0, per_round * sizeof(unsigned), s.stream));
   const long long work = (long long)n_mat * ((long long)((npair + 1) / 2) * (npair + 1) +
                                              (W ? (long long)npair * P : 0) + (vec ? npair : 0));
-  const int g_round = grid_for(work);
+  const int g_round = grid_for(work, kRoundThreads);
   const int norm_cols = std::max(1, std::min(64, (int)(((long long)P * P + 4095) / 4096)));
   double2* last = slots + (size_t)(P - 1) * per_round;
   cudaGraph_t graph = nullptr;
@@ -694,10 +714,11 @@ swkb_status jacobi(Scratch& s, double* A, double* W, double2* vec, int P, int n_
     const double2* cur = slots + (size_t)r * per_round;
     double2* nxt = slots + (size_t)(r + 1) * per_round;   // slot P - 1 after the last round
     if (W)
-      k_round<true><<<g_round, kThreads, 0, s.stream>>>(A, W, vec, P, n_mat, r, cur, nxt, cnt);
+      k_round<true><<<g_round, kRoundThreads, 0, s.stream>>>(A, W, vec, P, n_mat, r, cur, nxt,
+                                                              cnt);
     else
-      k_round<false><<<g_round, kThreads, 0, s.stream>>>(A, nullptr, vec, P, n_mat, r, cur, nxt,
-                                                          cnt);
+      k_round<false><<<g_round, kRoundThreads, 0, s.stream>>>(A, nullptr, vec, P, n_mat, r, cur,
+                                                               nxt, cnt);
   }
   cudaMemsetAsync(norms, 0, 2 * sizeof(double) * n_mat, s.stream);
   k_norms<<<dim3(norm_cols, n_mat), kThreads, 0, s.stream>>>(A, P, norms);
