@@ -748,6 +748,10 @@ swkb_status jacobi(Scratch& s, double* A, double* W, double2* vec, int P, int n_
       return hfail(SWKB_ERR_INVALID_ARG, "matrix %d has non-finite entries", m);
   }
   const size_t sweep_log = (size_t)(P - 1) * per_round;
+  // SWKB_HILL_LOG_SWEEPS: the log's first capacity in sweeps (tests set it
+  // to 1 to exercise its growth)
+  const char* lc = getenv("SWKB_HILL_LOG_SWEEPS");
+  const int first_cap = lc ? std::max(1, atoi(lc)) : 8;
   double2* logbuf = nullptr;
   int log_cap = 0;
   int sweeps = 0;
@@ -760,7 +764,7 @@ swkb_status jacobi(Scratch& s, double* A, double* W, double2* vec, int P, int n_
     HCK(cudaGraphLaunch(s.sweep, s.stream));
     if (log) {
       if (sweeps == log_cap) {   // room for twice as many sweeps (8 at first)
-        const int cap = std::max(8, 2 * log_cap);
+        const int cap = log_cap ? 2 * log_cap : first_cap;
         double2* grown = nullptr;
         HTRY(s.alloc(&grown, (size_t)cap * sweep_log));
         if (logbuf)

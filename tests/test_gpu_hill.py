@@ -269,3 +269,39 @@ def test_gaussian_duct_200km():
     d = swkb.hill_desc(w.BC_PERIODIC, pb.z_a, pb.z_b, pb.n_z, K, n_q, z_sym=0.0)
     got = swkb.swkb_hill_propagate(d, [pb.k], e[None], pb.u0[None], [200_000.0])
     assert rel_l2(got[0, 0], want[0]) < field_tol(pb.k, 200_000.0)
+
+
+def test_batch_of_periodic_layers_at_several_ranges():
+    """Two symmetric layers (both parities, so four matrices) at two ranges
+    in one call: each (problem, range) equals its own oracle run."""
+    k, L, n_z, K = 2.0 * math.pi, 64.0, 512, 80
+    n_q = 2 * K
+    s = L / 2 + np.arange(n_q + 1) * L / (2 * n_q)
+    z = np.arange(n_z) * L / n_z
+    xs = [7.0, 31.0]
+    ks, epss, u0s = [], [], []
+    for b, (a, w0) in enumerate(((0.02, 3.0), (-0.015, 4.5))):
+        f = lambda t, a=a: 1.0 + a * np.exp(-0.01 * (t - L / 2) ** 2)
+        ks.append(k * (1.0 + 0.1 * b))
+        epss.append(f(s))
+        u0s.append(np.exp(-((z - 24.0 - 5 * b) / w0) ** 2) * np.exp(1j * 0.2 * k * z))
+    d = swkb.hill_desc(w.BC_PERIODIC, 0.0, L, n_z, K, n_q, z_sym=L / 2)
+    got = swkb.swkb_hill_propagate(d, ks, np.array(epss), np.array(u0s), xs)
+    for b in range(2):
+        want = H.propagate(ks[b], epss[b], u0s[b], xs, H.BC_PERIODIC, 0.0, L, K, z_c=L / 2)
+        for r, x in enumerate(xs):
+            assert rel_l2(got[b, r], want[r]) < field_tol(ks[b], x), (b, x)
+
+
+def test_rotation_log_growth(monkeypatch):
+    """The rotation log starts with room for one sweep (test knob) and grows
+    at sweeps 1, 2 and 4: the fields equal those of the default capacity bit
+    for bit."""
+    pb, eps, u0 = _duct(n_z=512, height=25.0)
+    K, n_q = 96, 192
+    s = np.arange(n_q + 1) * 25.0 / n_q
+    d = swkb.hill_desc(w.BC_NEUMANN, 0.0, 25.0, 512, K, n_q)
+    want = swkb.swkb_hill_propagate(d, [pb.k], eps(s)[None], u0[None], [80.0])
+    monkeypatch.setenv("SWKB_HILL_LOG_SWEEPS", "1")
+    got = swkb.swkb_hill_propagate(d, [pb.k], eps(s)[None], u0[None], [80.0])
+    assert np.array_equal(got, want)
