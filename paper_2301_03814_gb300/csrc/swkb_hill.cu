@@ -432,14 +432,12 @@ __global__ void k_round(double* __restrict__ A, double* __restrict__ W,
                       (long long)gridDim.x * blockDim.x);
 }
 
-// Replays logged rotations on complex vectors, one CTA per vector held in
-// shared memory: FORWARD applies v <- J^T v round by round (v <- W v), the
-// reverse applies v <- J v from the last round back (v <- W^T v).  Each
-// thread fetches its next round's rotations before the current round's
-// barrier.
+// Replays the logged rotations backwards on complex vectors, v <- J v from
+// the last round to the first (v <- W^T v), one CTA per vector held in
+// shared memory.  Each thread fetches its next round's rotations before the
+// current round's barrier.
 constexpr int kReplayMaxPerThread = 4;
 
-template <bool FORWARD>
 __global__ void k_replay(const double2* __restrict__ log, int n_rounds, int P, int n_mat,
                          int vecs_per_mat, double2* __restrict__ vecs) {
   extern __shared__ double2 v[];
@@ -448,8 +446,7 @@ __global__ void k_replay(const double2* __restrict__ log, int n_rounds, int P, i
   double2* gv = vecs + (size_t)vec * P;
   for (int i = threadIdx.x; i < P; i += blockDim.x) v[i] = gv[i];
   auto rot_at = [&](int step, int i) {
-    const int g = FORWARD ? step : n_rounds - 1 - step;
-    return log[((size_t)g * n_mat + mat) * npair + i];
+    return log[((size_t)(n_rounds - 1 - step) * n_mat + mat) * npair + i];
   };
   double2 cur[kReplayMaxPerThread];
   for (int k = 0; k < kReplayMaxPerThread; ++k) {
@@ -458,8 +455,7 @@ __global__ void k_replay(const double2* __restrict__ log, int n_rounds, int P, i
   }
   __syncthreads();
   for (int step = 0; step < n_rounds; ++step) {
-    const int g = FORWARD ? step : n_rounds - 1 - step;
-    const int r = g % (P - 1);
+    const int r = (n_rounds - 1 - step) % (P - 1);
     double2 nxt[kReplayMaxPerThread];
     for (int k = 0; k < kReplayMaxPerThread; ++k) {
       const int i = threadIdx.x + k * blockDim.x;
@@ -472,13 +468,8 @@ __global__ void k_replay(const double2* __restrict__ log, int n_rounds, int P, i
       rr_pair(r, i, P, p, q);
       const double c = cur[k].x, s = cur[k].y;
       const double2 vp = v[p], vq = v[q];
-      if (FORWARD) {
-        v[p] = make_double2(c * vp.x - s * vq.x, c * vp.y - s * vq.y);
-        v[q] = make_double2(s * vp.x + c * vq.x, s * vp.y + c * vq.y);
-      } else {
-        v[p] = make_double2(c * vp.x + s * vq.x, c * vp.y + s * vq.y);
-        v[q] = make_double2(c * vq.x - s * vp.x, c * vq.y - s * vp.y);
-      }
+      v[p] = make_double2(c * vp.x + s * vq.x, c * vp.y + s * vq.y);
+      v[q] = make_double2(c * vq.x - s * vp.x, c * vq.y - s * vp.y);
     }
     for (int k = 0; k < kReplayMaxPerThread; ++k) cur[k] = nxt[k];
     __syncthreads();
@@ -675,6 +666,17 @@ struct Scratch {
     *p = (T*)v;
     return SWKB_OK;
   }
+  // frees one buffer now, after the stream's work on it
+  swkb_status release(void* p) {
+    HCK(cudaStreamSynchronize(stream));
+    for (size_t i = 0; i < ptrs.size(); ++i)
+      if (ptrs[i] == p) {
+        ptrs.erase(ptrs.begin() + i);
+        HCK(cudaFree(p));
+        break;
+      }
+    return SWKB_OK;
+  }
 };
 
 // Rotations of every round of every sweep, in order, (c, s) per pair:
@@ -767,9 +769,11 @@ swkb_status jacobi(Scratch& s, double* A, double* W, double2* vec, int P, int n_
         const int cap = log_cap ? 2 * log_cap : first_cap;
         double2* grown = nullptr;
         HTRY(s.alloc(&grown, (size_t)cap * sweep_log));
-        if (logbuf)
+        if (logbuf) {
           HCK(cudaMemcpyAsync(grown, logbuf, (size_t)sweeps * sweep_log * sizeof(double2),
                               cudaMemcpyDeviceToDevice, s.stream));
+          HTRY(s.release(logbuf));
+        }
         logbuf = grown;
         log_cap = cap;
       }
@@ -794,20 +798,18 @@ swkb_status jacobi(Scratch& s, double* A, double* W, double2* vec, int P, int n_
   return SWKB_OK;
 }
 
-// v <- W v (forward) or W^T v for n_vec vectors of P complex values
-template <bool FORWARD>
-swkb_status replay(Scratch& s, const RotLog& log, int P, int n_mat, int vecs_per_mat,
-                   double2* vecs) {
+// v <- W^T v for vecs_per_mat vectors of P complex values per matrix
+swkb_status replay_back(Scratch& s, const RotLog& log, int P, int n_mat, int vecs_per_mat,
+                        double2* vecs) {
   const int npair = P / 2;
   const int threads = std::min(1024, std::max(32, (npair + 31) / 32 * 32));
   if ((npair + threads - 1) / threads > kReplayMaxPerThread)
     return hfail(SWKB_ERR_INVALID_ARG, "matrix too large for the rotation replay");
   const size_t smem = (size_t)P * sizeof(double2);
   if (smem > 48 * 1024)
-    HCK(cudaFuncSetAttribute(k_replay<FORWARD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem));
-  k_replay<FORWARD><<<n_mat * vecs_per_mat, threads, smem, s.stream>>>(log.d, log.rounds, P,
-                                                                       n_mat, vecs_per_mat, vecs);
+    HCK(cudaFuncSetAttribute(k_replay, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_replay<<<n_mat * vecs_per_mat, threads, smem, s.stream>>>(log.d, log.rounds, P, n_mat,
+                                                              vecs_per_mat, vecs);
   HCK(cudaGetLastError());
   return SWKB_OK;
 }
@@ -948,7 +950,7 @@ swkb_status hill_propagate(const swkb_hill_desc* d, int batch, const double* k,
   HTRY(jacobi(s, A, nullptr, uh, P, n_mat, nullptr, &lg));
   k_advance_coefficients<<<grid_for((long long)n_mat * n_x * P), kThreads, 0, s.stream>>>(
       A, uh, hd, n_mat, xd, n_x, ph);                     // a_j exp(i alpha_j x)
-  HTRY(replay<false>(s, lg, P, n_mat, n_x, ph));          // g = W^T (a exp(i alpha x))
+  HTRY(replay_back(s, lg, P, n_mat, n_x, ph));           // g = W^T (a exp(i alpha x))
   k_synthesize<<<grid_for((long long)n_out), kThreads, 0, s.stream>>>(ph, f, hd, batch, n_x, tab,
                                                                        out);
   if (lam) k_eigenvalues<<<grid_for((long long)batch * n_eig), kThreads, 0, s.stream>>>(
