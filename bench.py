@@ -392,6 +392,17 @@ def sov_measurement(swkb, dev, with_oracle):
                                    "cores": os.cpu_count(),
                                    "note": "numpy with its BLAS/LAPACK default thread pool"}
         out[name] = rec
+    # the paper's second experiment, E2-like, entirely on the GPU: the S-WKB
+    # error against this reference as the screen spacing falls
+    hi = w.hill_gaussian_duct_200km()
+    d = swkb.hill_desc(hi.bc, hi.z_a, hi.z_b, hi.n_z, hi.K, hi.n_q, z_sym=hi.z_c)
+    ref = swkb.swkb_hill_propagate(d, hi.k, hi.eps, hi.u0, hi.xs)[0, 0]
+    base = w.config_gaussian_duct_200km()
+    curve = {}
+    for n in (200, 400, 800):
+        got = swkb.Plan(base.with_(n_screens=n, dx=200_000.0 / n), swkb.SWKB_MIXED).propagate()
+        curve[f"{200_000.0 / n:.0f} m"] = rel_l2(got, ref)
+    out["gaussian_duct_200km_swkb_error_vs_spacing"] = curve
     return out
 
 

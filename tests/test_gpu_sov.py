@@ -112,3 +112,21 @@ def test_gaussian_duct_200km_error_falls_with_screen_spacing():
         print(f"200 km duct, {n} screens of {pb.dx:.0f} m: rel-L2 {errs[-1]:.3e}, "
               f"{dt * 1e3:.1f} ms")
     assert errs[0] > 2.0 * errs[1] > 4.0 * errs[2] and errs[2] < 2e-3
+
+
+def test_error_curve_against_the_gpu_reference():
+    """The same 200 km curve with the reference computed on the GPU
+    (swkb_hill_propagate, the separation-of-variables solver of Sec. 3.1):
+    it equals the CPU reference to the phase conditioning of a 200 km range
+    (1e-6), so the S-WKB errors agree with those above, and the whole
+    experiment runs on the GPU."""
+    base = w.config_gaussian_duct_200km()
+    cpu_ref = _layer_reference(base, 200_000.0)
+    hi = w.hill_gaussian_duct_200km()
+    d = swkb.hill_desc(hi.bc, hi.z_a, hi.z_b, hi.n_z, hi.K, hi.n_q, z_sym=hi.z_c)
+    gpu_ref = swkb.swkb_hill_propagate(d, hi.k, hi.eps, hi.u0, hi.xs)[0, 0]
+    assert rel_l2(gpu_ref, cpu_ref) < 1e-6
+    for n in (200, 800):
+        got = swkb.Plan(base.with_(n_screens=n, dx=200_000.0 / n), swkb.SWKB_MIXED).propagate()
+        e_gpu, e_cpu = rel_l2(got, gpu_ref), rel_l2(got, cpu_ref)
+        assert abs(e_gpu - e_cpu) < 1e-3 * e_cpu + 1e-6, (n, e_gpu, e_cpu)
