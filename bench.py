@@ -403,6 +403,12 @@ def sov_measurement(swkb, dev, with_oracle):
         got = swkb.Plan(base.with_(n_screens=n, dx=200_000.0 / n), swkb.SWKB_MIXED).propagate()
         curve[f"{200_000.0 / n:.0f} m"] = rel_l2(got, ref)
     out["gaussian_duct_200km_swkb_error_vs_spacing"] = curve
+    # the first experiment, E1-like: the 40 km lens in 40 screens of 1 km
+    hi = w.hill_gaussian_lens_40km()
+    d = swkb.hill_desc(hi.bc, hi.z_a, hi.z_b, hi.n_z, hi.K, hi.n_q, z_sym=hi.z_c)
+    ref = swkb.swkb_hill_propagate(d, hi.k, hi.eps, hi.u0, hi.xs)[0, 0]
+    got = swkb.Plan(w.config_gaussian_lens_40km(), swkb.SWKB_MIXED).propagate()
+    out["gaussian_lens_40km_swkb_error"] = rel_l2(got, ref)
     return out
 
 

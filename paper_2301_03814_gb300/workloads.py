@@ -484,6 +484,18 @@ def hill_gaussian_duct_200km(n_q=4096, extra_modes=100):
                       pb.n_max + extra_modes, eps, pb.k, pb.u0, [200_000.0])
 
 
+def hill_gaussian_lens_40km(n_q=4096, extra_modes=100):
+    """The 600 m periodic domain with the single-focus Gaussian lens at its
+    centre (eps = 1 + 1e-4 exp(-1e-4 z^2), lambda = 5 cm, 60 m beam), 40 km,
+    K = n_max + extra_modes, eps even about z_c = 0."""
+    pb = config_gaussian_lens_40km()
+    L = pb.z_b - pb.z_a
+    s = np.arange(n_q + 1) * L / (2 * n_q)
+    eps = f_gaussian(pb.meta["a"], pb.meta["b"])(s)[0]
+    return HillInputs("hill-gaussian-lens-40km", BC_PERIODIC, pb.z_a, pb.z_b, 0.0,
+                      pb.n_max + extra_modes, eps, pb.k, pb.u0, [40_000.0])
+
+
 WORKLOADS = {
     "unit-periodic-512": config_unit_periodic,
     "surface-duct-16384": config_surface_duct,

@@ -130,3 +130,16 @@ def test_error_curve_against_the_gpu_reference():
         got = swkb.Plan(base.with_(n_screens=n, dx=200_000.0 / n), swkb.SWKB_MIXED).propagate()
         e_gpu, e_cpu = rel_l2(got, gpu_ref), rel_l2(got, cpu_ref)
         assert abs(e_gpu - e_cpu) < 1e-3 * e_cpu + 1e-6, (n, e_gpu, e_cpu)
+
+
+def test_lens_40km_against_the_gpu_reference():
+    """The 40 km lens (E1-like) against the GPU reference: the same
+    5.4e-5 / 5.6e-5 error as against the CPU reference."""
+    pb = w.config_gaussian_lens_40km()
+    cpu_ref = _layer_reference(pb, pb.dx * pb.n_screens)
+    hi = w.hill_gaussian_lens_40km()
+    d = swkb.hill_desc(hi.bc, hi.z_a, hi.z_b, hi.n_z, hi.K, hi.n_q, z_sym=hi.z_c)
+    gpu_ref = swkb.swkb_hill_propagate(d, hi.k, hi.eps, hi.u0, hi.xs)[0, 0]
+    assert rel_l2(gpu_ref, cpu_ref) < 1e-7
+    got = swkb.Plan(pb, swkb.SWKB_MIXED).propagate()
+    assert rel_l2(got, gpu_ref) < 2e-4
