@@ -369,8 +369,8 @@ void swkb_server_destroy(swkb_server* server);
  * Frobenius norm of every matrix is at most 1e-15 of its Frobenius norm.
  * on_device = 1: A, lambda_out and vectors_out are device pointers, ordered
  * on cuda_stream (NULL = the legacy default stream); 0: host pointers.  The
- * call allocates its workspace (about 3 batch n^2 doubles) per call, blocks
- * until done, and leaves A unchanged.  Errors: SWKB_ERR_INVALID_ARG (NULL,
+ * call allocates its workspace (about 2 batch n^2 doubles, 3 with vectors)
+ * per call, blocks until done, and leaves A unchanged.  Errors: SWKB_ERR_INVALID_ARG (NULL,
  * batch < 1, n < 1 or n > 8192, non-finite entries: no convergence),
  * SWKB_ERR_OOM, SWKB_ERR_CUDA.
  */
@@ -406,7 +406,9 @@ typedef struct {
  * block (K), each in no particular order; n_eig = K + 1 (Neumann), K
  * (Dirichlet), 2 K + 1 (periodic).  on_device = 1: eps, u0, u_out and
  * lambda_out are device pointers, ordered on cuda_stream; 0: host.
- * Allocates its workspace per call and blocks until done.  Errors:
+ * Allocates its workspace per call (per parity block and problem the matrix
+ * and the log of its rotations, about 10 K^2 doubles) and blocks until
+ * done.  Errors:
  * SWKB_ERR_INVALID_ARG (NULL, sizes, K or n_q out of range, z_sym off the
  * grid, k <= 0, x < 0, non-finite eps), SWKB_ERR_OOM, SWKB_ERR_CUDA.
  */
