@@ -16,9 +16,10 @@ events.  e2e times the same propagation through the C ABI with host buffers
 (pinned), copies included.
 
 --impl reference times the FP64 CPU oracle (the only other implementation of
-the method) on a bounded sample of the same workload: one screen with every
-8th plane-wave mode, scaled by the mode count (its cost is linear in the
-number of modes).
+the method) on the same workload, spread over every host core
+(oracle.swkb_parallel: bit-identical to the serial oracle): each step is one
+whole screen, its time measured directly (no extrapolation).  The same
+measurement, one screen, is the cpu_baseline key of the GPU line.
 """
 from __future__ import annotations
 
@@ -38,11 +39,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "screen-points/s (N_z*screens/s), mixed FP32/FP64 path"
 UNIT = "screen-points/s"
-ORACLE_MODE_STRIDE = 8
 SMI_FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-FP32_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz (max SM clock)"
 
 
 def parse_args():
@@ -54,6 +53,8 @@ def parse_args():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-paper-scale", action="store_true",
+                    help="skip the paper-scale 2000-screen run (key paper_scale)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="default launch shapes instead of the autotuned ones (for profiling)")
     ap.add_argument("--tiling", default=None, metavar="TILE,CTAS,N1",
@@ -83,56 +84,73 @@ def config_dict(pb, extra=None):
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle sample
+# CPU oracle on every host core
 # ---------------------------------------------------------------------------
-def oracle_sample_time(pb, stride=ORACLE_MODE_STRIDE):
-    """Seconds for one oracle screen over every stride-th mode, and the modes."""
-    from oracle.swkb_oracle import Oracle
-    o = Oracle(pb)
-    o.n = o.n[::stride]
-    o.kappa = o.kappa[::stride]
-    u = o.extend(pb.u0)
-    t = time.perf_counter()
-    o.screen(u, 0)
-    return time.perf_counter() - t, len(o.n), o.g.M
+def host_cpu():
+    """CPU model and the cores this process may use."""
+    from oracle.swkb_parallel import host_cores
+    model = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            key = line.split(":")[0].strip().lower()
+            if key in ("model name", "cpu model", "hardware") and ":" in line:
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    return model, host_cores()
 
 
-def cpu_baseline(pb, steps=1):
+def oracle_screens(pb, n_steps):
+    """Seconds of each of n_steps whole oracle screens (screens 0, 1, ... of
+    the workload, each from the field the previous one produced), with the
+    oracle on every host core."""
+    from oracle.swkb_parallel import ParallelOracle
     ts = []
-    for _ in range(steps):
-        dt, m_used, m_all = oracle_sample_time(pb)
-        ts.append(dt * m_all / m_used)
-    t_screen = statistics.mean(ts)
-    return {"value": pb.n_z / t_screen, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"1 screen of the same workload over every {ORACLE_MODE_STRIDE}th mode "
-                      f"({m_used} of {m_all}), time scaled by {m_all}/{m_used} (cost is linear "
-                      f"in the mode count); numpy FP64, single thread"}
+    with ParallelOracle(pb) as o:
+        u = o.extend(pb.u0)
+        for q in range(n_steps):
+            t = time.perf_counter()
+            u = o.screen(u, q)
+            ts.append(time.perf_counter() - t)
+        workers = o.workers
+    return ts, workers
+
+
+def cpu_baseline(pb):
+    ts, workers = oracle_screens(pb, 1)
+    model, _ = host_cpu()
+    return {"value": pb.n_z / ts[0], "unit": UNIT, "cores": workers, "kind": "oracle",
+            "cpu": model,
+            "sample": f"1 whole screen of the same workload (all {pb.n_z} points, all modes), "
+                      f"timed directly; numpy FP64 oracle on {workers} worker processes "
+                      f"(one per host core), bit-identical to the serial oracle"}
 
 
 def run_reference(args, rank, world):
     pb = workload()
     if rank != 0:
         return 0
-    for _ in range(args.warmup):
-        oracle_sample_time(pb)
-    ts, raw = [], []
-    for _ in range(args.steps):
-        dt, m_used, m_all = oracle_sample_time(pb)
-        raw.append(dt)
-        ts.append(dt * m_all / m_used)
-    t_screen = statistics.mean(ts)
-    value = pb.n_z / t_screen
+    ts, workers = oracle_screens(pb, args.warmup + args.steps)
+    ts = ts[args.warmup:]
+    value = pb.n_z * len(ts) / sum(ts)
+    model, _ = host_cpu()
     # the same metric and config as the GPU arm's line (the sample is in cpu_baseline)
     line = {"impl": "reference", "metric": METRIC,
             "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": statistics.mean(raw) * 1e3,
+            "warmup": args.warmup, "ms_per_step": statistics.mean(ts) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": config_dict(pb, {"parallelism": f"replicas x{world}" if world > 1
                                        else "single GPU"}),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"each step: 1 screen over every {ORACLE_MODE_STRIDE}th "
-                                       f"mode, scaled by the mode count"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
+                             "cpu": model,
+                             "sample": f"each step: 1 whole screen (screens {args.warmup}.."
+                                       f"{args.warmup + args.steps - 1} of the workload), "
+                                       f"numpy FP64 oracle on {workers} worker processes"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -229,10 +247,19 @@ def rel_l2(a, b):
 
 
 def march_flops_per_ray(pb):
-    # algorithmic flops of one ray (FMA = 2): per RK4 stage the medium
-    # (quintic value + 2 derivatives, interval lookup, reflection: 39) and the
-    # x-form right-hand side of the ray and variational system (33), plus the
-    # RK4 combination (15); launch / landing evaluations and the amplitude (100)
+    """Algorithmic work of one ray (the march's unit) by the count the scope
+    table gives for step (a2): per RK4 stage the permittivity quintic (~30
+    flops) and the ODE right-hand side (~45), one square root and one
+    division (1 flop each); four stages per step, N_t steps."""
+    return 4 * pb.rk4_steps * (30 + 45 + 1 + 1)
+
+
+def march_flops_per_ray_detailed(pb):
+    """The same work counted operation by operation (FMA = 2): per stage the
+    medium (quintic value and two derivatives, interval lookup, reflection:
+    39), the x-form right-hand side of the ray and variational system (33)
+    and the RK4 combination (15); launch / landing evaluations and the
+    amplitude (100).  Reported beside the headline count."""
     return 4 * pb.rk4_steps * (39 + 33 + 15) + 100
 
 
@@ -240,6 +267,31 @@ def resum_flops_per_term():
     # Newton-form interpolation of phase and amplitude (15), exact integer
     # phase + reduction (5), sincos (2), complex multiply-accumulate (10)
     return 32
+
+
+# special-function unit: sine and cosine of every (mode, point) term, at a
+# nominal 16 MUFU operations per SM and clock
+MUFU_PER_TERM = 2
+MUFU_PER_SM_CLK = 16
+
+
+def device_peaks(dev_index, sm_max_mhz):
+    """FP32, FP64 and MUFU peaks derived from the device's queried SM count
+    and its maximum SM clock (nvidia-smi, sampled during the run): 128 FP32
+    lanes (2 flops per FMA), 2 FP64 FMAs (the rate ncu reports for this
+    part) and 16 MUFU operations per SM and clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev_index).multi_processor_count
+    ghz = (sm_max_mhz or 0.0) / 1e3
+    src = (f"derived: {sms} SMs (queried) x {{}} x {ghz:.3f} GHz "
+           f"(maximum SM clock, nvidia-smi)")
+    return {"sms": sms, "ghz": ghz,
+            "fp32_tflops": sms * 128 * 2 * ghz / 1e3,
+            "fp32_src": src.format("128 FP32 lanes x 2 flop/FMA"),
+            "fp64_tflops": sms * 2 * 2 * ghz / 1e3,
+            "fp64_src": src.format("2 DFMA/clk x 2 flop"),
+            "mufu_tops": sms * MUFU_PER_SM_CLK * ghz / 1e3,
+            "mufu_src": src.format(f"{MUFU_PER_SM_CLK} MUFU ops/clk (nominal)")}
 
 
 def kernel_traffic(kind):
@@ -349,6 +401,56 @@ def batched_measurement(swkb, n=64, screens=10, seed=4):
     return {"instances": n, "screens_each": screens, "ok": int(sum(x == 0 for x in sts)),
             "screen_points_per_s": pts / dt, "wall_s": dt,
             "draw": "C4: f U(1,10) GHz, H U(100,400) m, N_z 2^12..2^16, seed 4"}
+
+
+def paper_scale_measurement(swkb, dev):
+    """The largest single-GPU configuration, the paper-scale range-dependent
+    duct (500 m, N_z = 131072, 1395 modes, 100 km in 2000 screens, 101 table
+    columns): one full 2000-screen mixed propagation (autotuned plan, graph
+    captured by one warm-up run), CUDA events on its stream around the timed
+    run; then the first 100 screens in FP64 and mixed and the rel-L2 between
+    them."""
+    import torch
+    from paper_2301_03814_gb300 import workloads as w
+    pb = w.config_range_dependent_duct()
+    stream = torch.cuda.Stream(device=dev)
+    u0 = torch.from_numpy(pb.u0).to(dev)
+    out = torch.empty_like(u0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    plan = swkb.Plan(pb, swkb.SWKB_MIXED, stream=stream.cuda_stream, device=dev.index,
+                     autotune=True)
+    plan.propagate_device(u0.data_ptr(), out.data_ptr())          # warm-up, graph capture
+    torch.cuda.synchronize()
+    e0.record(stream)
+    plan.propagate_device(u0.data_ptr(), out.data_ptr())
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    info = plan.info
+    finite = bool(torch.isfinite(torch.view_as_real(out)).all())
+    d100 = torch.empty_like(u0)
+    plan.propagate_device(u0.data_ptr(), d100.data_ptr(), n_screens=100)
+    mixed100 = d100.cpu().numpy()
+    plan.close()
+    plan64 = swkb.Plan(pb, swkb.SWKB_FP64, stream=stream.cuda_stream, device=dev.index)
+    e0.record(stream)
+    plan64.propagate_device(u0.data_ptr(), d100.data_ptr(), n_screens=100)
+    e1.record(stream)
+    e1.synchronize()
+    ms64 = e0.elapsed_time(e1)
+    fp64_100 = d100.cpu().numpy()
+    plan64.close()
+    return {"workload": pb.name, "n_z": pb.n_z, "n_fft": info.n_fft, "modes": info.n_modes,
+            "screens": pb.n_screens, "table_columns": int(pb.profile.n_cols),
+            "ms": ms, "screen_points_per_s": pb.n_z * pb.n_screens / (ms / 1e3),
+            "finite": finite,
+            "tiling": {"tile_points": info.tile_points, "ctas_per_sm": info.ctas_per_sm,
+                       "fft_n1": info.fft_n1},
+            "fp64_100_screens_ms": ms64,
+            "fp64_screen_points_per_s": pb.n_z * 100 / (ms64 / 1e3),
+            "mixed_vs_fp64_rel_l2_100_screens": rel_l2(mixed100, fp64_100),
+            "timing": "CUDA events around one full propagation (graph captured by a warm-up "
+                      "run); inputs resident"}
 
 
 def sov_measurement(swkb, dev, with_oracle):
@@ -523,40 +625,73 @@ def run_ours(args, world, rank, local):
     e2e = {"value": points_per_step * world / t_e2e, "unit": UNIT,
            "h2d_bytes_per_step": int(h_in.numel() * 16), "d2h_bytes_per_step": int(h_out.numel() * 16)}
 
-    # FP64 march against the FP64 peak (2 DFMA per SM per clock, the rate ncu
-    # reports): events around every FP64 launch of the FP64 steps
-    peak_fp64 = 152 * 2 * 2 * 2.07e9 / 1e12
+    # peaks from the queried SM count and the sampled maximum SM clock
+    smi_max = (clk or {}).get("sm_max_mhz")
+    if not smi_max:
+        try:
+            smi_max = float(subprocess.check_output(
+                ["nvidia-smi", f"--id={local}", "--query-gpu=clocks.max.sm",
+                 "--format=csv,noheader,nounits"], text=True).strip().splitlines()[0])
+        except (OSError, ValueError, subprocess.CalledProcessError, IndexError):
+            smi_max = None
+    pk = device_peaks(local, smi_max)
+
+    # FP64 march against the FP64 peak: events around every FP64 launch of
+    # the FP64 steps
     fp64_roof = None
     info64 = plan64.info
+    rays64 = info64.march_modes * info64.n_rays_total
     if st64["kernel_timed"]["march"]:
         per64 = st64["kernel_ms"]["march"] / 1e3 / st64["kernel_timed"]["march"]
-        ach64 = march_flops_per_ray(pb) * info64.march_modes * info64.n_rays_total / per64 / 1e12
-        fp64_roof = {"bound": "alu", "achieved": ach64, "peak": peak_fp64, "unit": "TFLOP/s",
-                     "frac": ach64 / peak_fp64, "launch_ms": per64 * 1e3,
-                     "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"}
+        ach64 = march_flops_per_ray(pb) * rays64 / per64 / 1e12
+        fp64_roof = {"bound": "alu", "achieved": ach64, "peak": pk["fp64_tflops"],
+                     "unit": "TFLOP/s", "frac": ach64 / pk["fp64_tflops"],
+                     "frac_detailed_count": march_flops_per_ray_detailed(pb) * rays64 / per64
+                     / 1e12 / pk["fp64_tflops"],
+                     "launch_ms": per64 * 1e3, "peak_source": pk["fp64_src"]}
 
     # roofline of the dominant kernel (live event times of the timed region)
     kms = st["kernel_ms"]
     kl = st["kernel_launches"]
     info = plan.info
-    peak_fp32 = 152 * 128 * 2 * 2.07e9 / 1e12
+    rays = info.march_modes * info.n_rays_total
+    terms = info.n_modes * info.resum_points
     if dom == "march":
-        work = march_flops_per_ray(pb) * info.march_modes * info.n_rays_total
+        work = march_flops_per_ray(pb) * rays
+        work_detailed = march_flops_per_ray_detailed(pb) * rays
+        unit_note = (f"{rays} rays ({info.march_modes} marched modes x {info.n_rays_total} rays) "
+                     f"x {march_flops_per_ray(pb)} flops (4 N_t (30 + 45 + sqrt + div))")
     elif dom == "resum":
-        work = resum_flops_per_term() * info.n_modes * info.resum_points
+        work = work_detailed = resum_flops_per_term() * terms
+        unit_note = f"{terms} terms x {resum_flops_per_term()} flops"
     else:
-        work = None
+        work = work_detailed = None
+        unit_note = None
     roofline = None
     kt = st["kernel_timed"]
     if work is not None and kt[dom]:
         per_launch_s = kms[dom] / 1e3 / kt[dom]
         achieved = work / per_launch_s / 1e12
-        roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_fp32,
-                    "unit": "TFLOP/s", "frac": achieved / peak_fp32,
+        roofline = {"bound": "alu", "kernel": dom, "achieved": achieved,
+                    "peak": pk["fp32_tflops"], "unit": "TFLOP/s",
+                    "frac": achieved / pk["fp32_tflops"],
                     "traffic": kernel_traffic(dom),
-                    "peak_source": f"derived: {FP32_PEAK_NOTE}",
-                    "work_per_launch": work, "launch_ms": per_launch_s * 1e3,
+                    "peak_source": pk["fp32_src"],
+                    "work_per_launch": work, "work_unit": unit_note,
+                    "frac_detailed_count": work_detailed / per_launch_s / 1e12
+                    / pk["fp32_tflops"],
+                    "launch_ms": per_launch_s * 1e3,
                     "timed_launches": int(kt[dom]), "launches": int(kl[dom])}
+    # the resummation against the special-function unit (two MUFU operations
+    # per term), from the serialised per-kernel breakdown step
+    resum_roof = None
+    if breakdown["kernel_timed"]["resum"]:
+        per_r = breakdown["kernel_ms"]["resum"] / 1e3 / breakdown["kernel_timed"]["resum"]
+        ach_r = MUFU_PER_TERM * terms / per_r / 1e12
+        resum_roof = {"bound": "mufu", "achieved": ach_r, "peak": pk["mufu_tops"],
+                      "unit": "Tops/s", "frac": ach_r / pk["mufu_tops"],
+                      "terms_per_launch": terms, "launch_ms": per_r * 1e3,
+                      "peak_source": pk["mufu_src"]}
     share = {k: round(v / max(sum(kms_all.values()), 1e-30), 4) for k, v in kms_all.items()}
 
     if rank != 0:
@@ -578,7 +713,8 @@ def run_ours(args, world, rank, local):
             "kernel_ms_per_step": kms_all,
             "kernel_ms_per_step_note": "one extra step, march serialised onto the plan stream, "
                                        "events around every launch",
-            "kernel_share": share, "roofline": roofline, "clocks": clk,
+            "kernel_share": share, "roofline": roofline, "resum_roofline": resum_roof,
+            "clocks": clk,
             "step_ms": {"p50": statistics.median(ts), "p99": float(np.percentile(ts, 99)),
                         "min": min(ts), "max": max(ts)}}
     if world == 1 and not args.no_serving:
@@ -587,6 +723,8 @@ def run_ours(args, world, rank, local):
         line["batched"] = batched_measurement(swkb)
     if world == 1 and not args.no_serving:
         line["sov_reference"] = sov_measurement(swkb, dev, not args.no_cpu_baseline)
+    if world == 1 and not args.no_paper_scale:
+        line["paper_scale"] = paper_scale_measurement(swkb, dev)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(pb)
     print(json.dumps(line), flush=True)

@@ -285,8 +285,10 @@ swkb_status swkb_plan_get_stats(const swkb_plan* plan, swkb_plan_stats* stats);
  * with SWKB_ERR_INVALID_ARG, as are host pointers.  The call is asynchronous
  * on cuda_stream (NULL = the default stream).
  *
- * The working storage is a fixed set of file-scope device arrays (about
- * 2.5 MB) that every GPU loading this library holds until the process exits.
+ * The working storage is a fixed set of file-scope device arrays (3 MB:
+ * the pass-1 intermediate, the twiddles and one unit phase per mode, each
+ * 65536 complex128 values) that every GPU loading this library holds until
+ * the process exits.
  * The first call on a device performs a one-time set-up on that device (it
  * resolves the arrays' device addresses, initialises one of them and
  * synchronises the device); make that first call before any stream capture.

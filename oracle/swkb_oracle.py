@@ -414,14 +414,21 @@ class Oracle:
         sum_n c_n A_n exp(i (k kappa_n (z_m - z_lo) + k r_n))."""
         g = self.g
         delta = (rays["z"] - g.z_lo) / g.dz
-        m = np.arange(g.N)
         out = np.zeros(g.N, dtype=np.complex128)
         for i in range(len(self.n)):
-            r_m, a_m = self.interpolate(delta[i], (rays["r"][i], rays["a"][i]))
-            n = int(self.n[i])
-            base = 2.0 * math.pi * ((n * m) % g.N) / g.N             # = k kappa_n (z_m - z_lo)
-            out += c[i] * a_m * np.exp(1j * (base + self.pb.k * r_m))
+            out += self.mode_term(int(self.n[i]), c[i], delta[i], rays["r"][i], rays["a"][i])
         return out
+
+    def mode_term(self, n: int, c_n: complex, delta: np.ndarray, r: np.ndarray,
+                  a: np.ndarray) -> np.ndarray:
+        """One mode's contribution to Eq. ray_bundle_q_plus_1 on the grid:
+        phase and amplitude interpolated from the rays' landings delta (R8),
+        c_n A_n(z_m) exp(i (k kappa_n (z_m - z_lo) + k r_n(z_m)))."""
+        g = self.g
+        m = np.arange(g.N)
+        r_m, a_m = self.interpolate(delta, (r, a))
+        base = 2.0 * math.pi * ((n * m) % g.N) / g.N                 # = k kappa_n (z_m - z_lo)
+        return c_n * a_m * np.exp(1j * (base + self.pb.k * r_m))
 
     # -- fields between screens (Section 2: extra interpolation points) --------------
     def screen_planes(self, u: np.ndarray, q: int, planes: int):

@@ -1261,7 +1261,11 @@ cudaError_t prepare_kernels(int resum_smem) {
 
 template <typename T>
 cudaError_t prepare_fft_kernels() {
-  return cudaSuccess;   // the DFT passes use no dynamic shared memory
+  // k_fft1's dynamic shared memory is (N1 FFT1_COLS + N1) complex values: at
+  // most 9 KB for the largest split the plans allow (N1 = 64), inside the
+  // default 48 KB limit; k_fft2 uses static shared memory only
+  static_assert((64 * FFT1_COLS + 64) * 16 <= 48 * 1024, "k_fft1 staging exceeds 48 KB");
+  return cudaSuccess;
 }
 
 template <typename T>

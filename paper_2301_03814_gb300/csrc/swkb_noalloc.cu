@@ -8,7 +8,7 @@
 // device and stall other streams).  Such callers still hand in their input
 // and output buffers; the FFT's working storage lives here instead, in
 // file-scope device arrays of a fixed size that every GPU loading this library
-// holds until the process exits (about 2.5 MB per device).
+// holds until the process exits (3 MB per device).
 //
 // The arithmetic is the library's FP64 pruned two-pass DFT (k_fft1 / k_fft2),
 // unchanged; only where its scratch comes from differs.
@@ -28,7 +28,8 @@ constexpr int kMaxN = 65536;   // largest FFT length accepted
 // returned by cudaGetSymbolAddress to the kernels.
 static __device__ __align__(256) double2 g_fft_mid[kMaxN];        // pass-1 output [N1][N2]
 static __device__ __align__(256) double2 g_twiddle[kMaxN];        // exp(-2 pi i k / N)
-static __device__ __align__(256) double2 g_unit_phase[kMaxN / 2];  // exp(i 0) per mode
+// one entry per kept mode: 2 n_max + 1 <= n_fft - 1 < kMaxN
+static __device__ __align__(256) double2 g_unit_phase[kMaxN];     // exp(i 0) per mode
 
 struct DeviceScratch {
   bool ready = false;
@@ -69,7 +70,7 @@ swkb_status setup(int dev, DeviceScratch** out) {
     if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&d.unit_phase, g_unit_phase);
     if (e == cudaSuccess) e = swkb::prepare_fft_kernels<double>();
     if (e == cudaSuccess) {
-      k_fill_unit<<<(kMaxN / 2 + 255) / 256, 256>>>(d.unit_phase, kMaxN / 2);
+      k_fill_unit<<<(kMaxN + 255) / 256, 256>>>(d.unit_phase, kMaxN);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();

@@ -18,6 +18,7 @@
 // Nothing waits on the device without the stream having been handed work;
 // host waits are condition variables with a bounded period.
 
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -35,7 +36,9 @@
 
 namespace {
 
-enum class RState { Queued, Resident, Done };
+// Queued: in the FIFO.  Admitting: taken off the FIFO by the worker, whose
+// plan is being created outside the lock.  Resident: on the device.
+enum class RState { Queued, Admitting, Resident, Done };
 
 struct Request {
   uint64_t ticket = 0;
@@ -127,6 +130,7 @@ void worker_main(swkb_server* s) {
         if (s->in_use + r->footprint > s->budget) break;   // FIFO: wait for memory
         s->queue.pop_front();
         s->in_use += r->footprint;
+        r->state = RState::Admitting;   // no longer in the queue: cancel only flags it
         admit.push_back(r);
       }
       if (s->resident.empty() && admit.empty()) {
@@ -134,7 +138,12 @@ void worker_main(swkb_server* s) {
         continue;
       }
     }
-    // create the admitted requests' plans (device allocation) outside the lock
+    // create the admitted requests' plans (device allocation) outside the lock;
+    // SWKB_ADMIT_DELAY_MS (a test hook) holds this window open for so long,
+    // so that a test can cancel a request while it is being admitted
+    if (!admit.empty())
+      if (const char* d = getenv("SWKB_ADMIT_DELAY_MS"))
+        std::this_thread::sleep_for(std::chrono::milliseconds(atoi(d)));
     for (Request* r : admit) {
       swkb_plan* plan = nullptr;
       swkb_status st = swkb_plan_create(&r->prof, r->k, &r->dom, r->n_z, r->dx, &r->opt, &plan);
@@ -353,9 +362,14 @@ swkb_status swkb_cancel(swkb_server* s, uint64_t ticket) {
   Request* r = it->second;
   if (r->state == RState::Done) return SWKB_OK;
   r->cancel = true;
+  // a queued request is completed here; one being admitted or resident is
+  // only flagged, and the worker, which still uses it, completes it
   if (r->state == RState::Queued) {
-    s->queue.erase(std::find(s->queue.begin(), s->queue.end(), r));
-    complete(s, r, SWKB_ERR_CANCELLED, "cancelled");
+    auto q = std::find(s->queue.begin(), s->queue.end(), r);
+    if (q != s->queue.end()) {
+      s->queue.erase(q);
+      complete(s, r, SWKB_ERR_CANCELLED, "cancelled");
+    }
   }
   s->cv_work.notify_all();
   return SWKB_OK;

@@ -214,3 +214,60 @@ def pin_planes_before_absorber(O, planes=4):
         ref = angular_spectrum(pb.u0, pb.k, g.L, j * pb.dx / planes, g.n_max, 1.0)
         err = max(err, rel_l2(rows[j - 1], ref))
     return err
+
+
+def x_only_ray(kappa, s, eps_a, slope, x):
+    """Closed-form ray of a permittivity that depends on x only, linear on the
+    stretch ridden, eps = eps_a + slope x (x from the launch): eps_z = 0 keeps
+    Q = kappa and Q_s = 0, so Z_s = 1; with P(x) = sqrt(eps(x) - kappa^2),
+    z - s = int kappa / P dx, r = int (eps - kappa Q) / P dx = int P dx and the
+    amplitude factor is sqrt(P0 / P1)."""
+    P0 = math.sqrt(eps_a - kappa * kappa)
+    P1 = math.sqrt(eps_a + slope * x - kappa * kappa)
+    if slope == 0.0:
+        dz, r = kappa * x / P0, P0 * x
+    else:
+        dz = 2.0 * kappa * (P1 - P0) / slope
+        r = 2.0 * (P1 ** 3 - P0 ** 3) / (3.0 * slope)
+    return dict(z=s + dz, Q=kappa, r=r, Zs=1.0, Qs=0.0, a=math.sqrt(P0 / P1))
+
+
+# eps of the two-screen x-only medium: columns at x = 0, D, D, 2 D (a jump at
+# the screen edge D: left limit first, then the right limit)
+X_ONLY_D = 20.0
+X_ONLY_EPS = (1.0, 1.06, 0.97, 1.012)
+
+
+def pin_x_only_columns(O, nt=64):
+    """Range-column weights and limits (reading R10) against closed forms.
+    The medium varies with x only, linearly between four columns at
+    x = 0, D, D, 2 D with a jump at D; screen 0 rides 0 -> D, screen 1
+    D -> 2 D.  Rays are stopped on the planes D/4, D/2, 3D/4 of each screen,
+    where eps comes from interior blends of two columns (a swapped blend
+    weight makes the profile run backwards there), and at the screen end, where
+    screen 0 must take the left limit of the jump and screen 1 start from the
+    right limit.  Returns the largest relative error of z - s, Q, r, Z_s, Q_s
+    and the amplitude factor."""
+    D = X_ONLY_D
+    k = 2.0 * math.pi
+    cols = [w.f_const(e) for e in X_ONLY_EPS]
+    prof = w._table([0.0, D, D, 2 * D], -64.0, 0.125, int(256 / 0.125) + 1, cols)
+    pb = w.Problem("x-only", k, 0.0, 64.0, 512, w.BC_PERIODIC, 0.0, D, 2, prof,
+                   np.zeros(512, complex), math.radians(30.0), 1, nt, 0.0)
+    o = O(pb)
+    kap = np.array([-0.4, -0.1, 0.0, 0.2, 0.45])
+    s = np.array([-5.0, 3.0, 10.0, 20.0, 33.0])
+    err = 0.0
+    for q, (ea, eb) in enumerate(((X_ONLY_EPS[0], X_ONLY_EPS[1]),
+                                  (X_ONLY_EPS[2], X_ONLY_EPS[3]))):
+        slope = (eb - ea) / D
+        for steps in (nt // 4, nt // 2, 3 * nt // 4, nt):
+            got = o.march(q, kap, s, steps=steps)
+            x = D * steps / nt
+            for i in range(len(kap)):
+                ref = x_only_ray(kap[i], s[i], ea, slope, x)
+                for key, scale in (("z", abs(ref["z"] - s[i]) + 1.0), ("Q", 1.0),
+                                   ("r", abs(ref["r"])), ("Zs", 1.0), ("Qs", 1.0),
+                                   ("a", 1.0)):
+                    err = max(err, abs(got[key][i] - ref[key]) / scale)
+    return err

@@ -195,3 +195,34 @@ def test_concurrent_submitters_and_pollers():
     srv.close()
     assert not errors, errors
     assert s["completed"] == 8 and s["failed"] == 0
+
+
+def test_cancel_while_being_admitted(monkeypatch):
+    """A request cancelled after the worker took it off the queue but before
+    its plan exists (the admission window, held open by a test hook) is
+    completed once as cancelled by the worker; the server's accounting
+    returns to zero and the next request is served."""
+    monkeypatch.setenv("SWKB_ADMIT_DELAY_MS", "400")
+    pb = w.config_surface_duct_small(n_screens=2)
+    srv = swkb.Server(8 * GB, max_slots=1)
+    st, t = srv.submit(pb, swkb.SWKB_MIXED)
+    assert st == swkb.SWKB_OK
+    t0 = time.perf_counter()
+    while True:   # taken off the queue, not yet resident
+        s = srv.stats()
+        if s["queued"] == 0 and s["resident"] == 0:
+            break
+        assert time.perf_counter() - t0 < 10.0
+        time.sleep(0.001)
+    assert srv.cancel(t) == swkb.SWKB_OK
+    assert srv.poll(t, timeout_ms=0)[0] == swkb.SWKB_NOT_READY   # still the worker's
+    st, _ = srv.poll(t, timeout_ms=30_000)
+    assert st == swkb.SWKB_ERR_CANCELLED
+    s = srv.stats()
+    assert s["failed"] == 1 and s["resident"] == 0 and s["hbm_in_use"] == 0
+    monkeypatch.delenv("SWKB_ADMIT_DELAY_MS")
+    st, t = srv.submit(pb, swkb.SWKB_MIXED)
+    st, got = srv.poll(t, timeout_ms=60_000)
+    assert st == swkb.SWKB_OK
+    assert np.array_equal(got, swkb.Plan(pb, swkb.SWKB_MIXED).propagate())
+    srv.close()

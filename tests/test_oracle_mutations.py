@@ -52,6 +52,40 @@ def _rhs_variant(kind):
     return V
 
 
+class SwappedBlendWeight(Oracle):        # th <-> 1 - th between range columns
+    def __init__(self, pb):
+        super().__init__(pb)
+        base = self.medium.column_weights
+
+        def swapped(x, right):
+            c, th = base(x, right)
+            return c, 1.0 - th
+        self.medium.column_weights = swapped
+
+
+class SwappedColumnLimits(Oracle):        # left limit at a screen start, right at its end
+    def __init__(self, pb):
+        super().__init__(pb)
+        base = self.medium.column_weights
+        self.medium.column_weights = lambda x, right: base(x, not right)
+
+
+class BlendWeightOnlyInside(Oracle):      # the blend formula itself with swapped weights
+    def __init__(self, pb):
+        super().__init__(pb)
+        m = self.medium
+        plain = m.eval
+
+        def ev(x, right, z):
+            c, th = m.column_weights(x, right)
+            if th in (0.0, 1.0):
+                return plain(x, right, z)
+            a = m.column_eval(c, z)
+            b = m.column_eval(c + 1, z)
+            return tuple(th * a[i] + (1.0 - th) * b[i] for i in range(3))
+        m.eval = ev
+
+
 class ConjugateDFT(Oracle):
     def modes(self, u):
         return np.fft.ifft(u)[self.n % self.g.N]
@@ -94,6 +128,7 @@ def _caught(O):
         lambda: P.pin_planes_homogeneous(O, bc=1) > 1e-12,
         lambda: P.pin_linear_ray_steps(O) > 1e-7,
         lambda: P.pin_planes_before_absorber(O) > 1e-12,
+        lambda: P.pin_x_only_columns(O) > 1e-9,
     ]
     for c in checks:
         try:
@@ -107,10 +142,12 @@ def _caught(O):
 @pytest.mark.parametrize("O", [NoSqrtAmplitude, SwappedP0P1, _rhs_variant("dQ-factor"),
                                _rhs_variant("dr-kappa2"), _rhs_variant("Ps-sign"),
                                _rhs_variant("Qs-drop"), ConjugateDFT, ShiftedOrigin,
-                               ShiftedStencil, PlanesMarchWholeScreen, PlanesWithAbsorber],
+                               ShiftedStencil, PlanesMarchWholeScreen, PlanesWithAbsorber,
+                               SwappedBlendWeight, SwappedColumnLimits, BlendWeightOnlyInside],
                          ids=["amp-no-sqrt", "P0-P1-swap", "dQ-factor", "dr-kappa2", "Ps-sign",
                               "Qs-drop", "conj-dft", "origin-shift", "stencil-shift",
-                              "planes-whole-screen", "planes-absorbed"])
+                              "planes-whole-screen", "planes-absorbed", "blend-swapped",
+                              "limits-swapped", "blend-formula-swapped"])
 def test_planted_mistake_is_caught(O):
     assert _caught(O)
 

@@ -52,6 +52,12 @@ def test_column_weights_left_right_limits():
     assert m.column_weights(500.0, False) == (2, 1.0)
 
 
+def test_x_only_medium_column_blend_and_limits():
+    """Linear-in-x blend between range columns and the left / right limits
+    at a jump on a screen edge, against closed-form rays (R10)."""
+    assert P.pin_x_only_columns(Oracle) < 1e-9
+
+
 def test_geometry_counts():
     g = geometry(w.config_unit_periodic())
     assert (g.N, g.n_max, g.M, g.G, g.NRT) == (512, 32, 65, 96, 704)

@@ -52,6 +52,27 @@ def test_noalloc_modes_match_allocating_path_twice(make):
         assert np.max(np.abs(got - want)) <= TOL * np.max(np.abs(want))
 
 
+@pytest.mark.parametrize("n_fft,n_max", [(64, 1), (64, 31), (65536, 1), (65536, 32767)])
+def test_noalloc_modes_at_the_size_limits_match_numpy(n_fft, n_max):
+    """The smallest and largest accepted lengths with the fewest and the most
+    kept modes (n_max = n_fft / 2 - 1 uses a unit phase per mode up to index
+    n_fft - 2), twice in a row, against numpy's FFT of a random field."""
+    torch = _torch()
+    rng = np.random.default_rng(n_fft + n_max)
+    n = np.arange(-n_max, n_max + 1)
+    u_dev = torch.empty(n_fft, dtype=torch.complex128, device="cuda")
+    c_dev = torch.empty(2 * n_max + 1, dtype=torch.complex128, device="cuda")
+    for _ in range(2):
+        field = rng.standard_normal(n_fft) + 1j * rng.standard_normal(n_fft)
+        want = np.fft.fft(field)[n % n_fft] / n_fft
+        u_dev.copy_(torch.from_numpy(field))
+        status = swkb.swkb_modes_noalloc(u_dev.data_ptr(), n_fft, n_max, c_dev.data_ptr())
+        assert status == swkb.SWKB_OK, swkb.swkb_last_error()
+        torch.cuda.synchronize()
+        got = c_dev.cpu().numpy()
+        assert np.max(np.abs(got - want)) <= TOL * np.max(np.abs(want))
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch_and_host_pointers():
     torch = _torch()
     u = torch.zeros(1 << 17, dtype=torch.complex128, device="cuda")
@@ -59,6 +80,8 @@ def test_noalloc_rejects_sizes_beyond_its_scratch_and_host_pointers():
     assert swkb.swkb_modes_noalloc(u.data_ptr(), 1 << 17, 31, c.data_ptr()) == \
         swkb.SWKB_ERR_INVALID_ARG
     assert "65536" in swkb.swkb_last_error()
+    assert swkb.swkb_modes_noalloc(u.data_ptr(), 512, 256, c.data_ptr()) == \
+        swkb.SWKB_ERR_INVALID_ARG
     host = np.zeros(2 * 512)
     assert swkb.swkb_modes_noalloc(host.ctypes.data, 512, 31, c.data_ptr()) == \
         swkb.SWKB_ERR_INVALID_ARG
