@@ -91,7 +91,15 @@ def host_cpu():
     from oracle.swkb_parallel import host_cores
     model = None
     try:
-        for line in open("/proc/cpuinfo"):
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in ([] if model else open("/proc/cpuinfo")):
             key = line.split(":")[0].strip().lower()
             if key in ("model name", "cpu model", "hardware") and ":" in line:
                 model = line.split(":", 1)[1].strip()
