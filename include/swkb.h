@@ -342,6 +342,77 @@ swkb_status swkb_server_get_stats(swkb_server* server, swkb_server_stats* stats)
 void swkb_server_destroy(swkb_server* server);
 
 /* ---------------------------------------------------------------------------
+ * Batched propagation in one persistent launch.  Many requests of uneven
+ * size (frequency, N_z, range, medium) are advanced screen by screen by ONE
+ * cooperative kernel launch (captured in a CUDA graph and replayed per run):
+ * every step of every screen of every request (Algorithm 1: the ray march,
+ * the two DFT passes, the landing brackets, the fused interpolation and modal
+ * sum; the extension of the input before the first screen and the final
+ * reduction and output) is a job of work items in one device queue, ordered
+ * so that each job's producers come earlier; persistent CTAs claim items in
+ * queue order and wait -- bounded -- on per-request counters of finished
+ * items.  Rays depend on the medium only, so each request's march runs one
+ * screen ahead of its field into three rotating ray buffers.  Each request
+ * keeps its own plan's arithmetic, launch shapes and summation orders: its
+ * field equals the one its plan computes alone, bit for bit.
+ * ------------------------------------------------------------------------- */
+typedef struct swkb_batch swkb_batch;   /* opaque, library-owned */
+
+typedef struct {
+  int32_t ctas_per_sm;    /* persistent CTAs per SM (0 = as many as fit)      */
+  int32_t wait_limit_ms;  /* bound of every wait of a work item on its
+                             producers (0 = 2000 ms); a wait that runs out
+                             abandons the launch with SWKB_ERR_TIMEOUT       */
+  int32_t device;         /* CUDA device ordinal                              */
+  void* cuda_stream;      /* cudaStream_t to run on; NULL = a library stream */
+} swkb_batch_options;
+
+typedef struct {
+  int32_t instances, precision;
+  int32_t grid, ctas_per_sm, threads;   /* the persistent launch's shape      */
+  int32_t jobs;                         /* jobs in the queue                  */
+  int64_t items;                        /* work items over all jobs           */
+  int32_t steps;                        /* screen steps (the longest request) */
+  size_t shared_bytes;                  /* dynamic shared memory per CTA      */
+  size_t device_bytes;                  /* device memory held by the batch    */
+} swkb_batch_info;
+
+/* Zeroes *opt (every field's default). */
+void swkb_batch_options_default(swkb_batch_options* opt);
+
+/*
+ * Build a batch of n requests (swkb_request as for the server: profile,
+ * wavenumber, domain, n_z, spacing, options, incident field u0 (host), q0,
+ * n_screens >= 1).  All requests share one precision (options->precision);
+ * each gets a plan with its own options (fixed launch shapes or autotune as
+ * requested; reuse_rays and planes are ignored; fft_n1 must be >= 2), its
+ * input field is copied to the device, and the batch allocates its queue,
+ * counters and a third ray-buffer set per request.  Errors: those of
+ * swkb_plan_create (message prefixed with the request index),
+ * SWKB_ERR_INVALID_ARG (n < 1, NULL, mixed precisions, n_screens < 1),
+ * SWKB_ERR_OOM, SWKB_ERR_CUDA.
+ */
+swkb_status swkb_batch_create(int32_t n, const swkb_request* reqs,
+                              const swkb_batch_options* opt, swkb_batch** out);
+
+/*
+ * Run every request of the batch, each from its input field on screen q0 to
+ * screen q0 + n_screens, in one persistent launch.  u_in: NULL (the fields
+ * given at creation, or those of the last run's u_in) or the requests'
+ * inputs concatenated in request order (sum of n_z complex128 values);
+ * u_out: the outputs, concatenated the same way (NULL: not returned).  Both
+ * are device pointers when on_device = 1, else host memory.  Blocks until
+ * done.  Errors: SWKB_ERR_TIMEOUT (a wait ran out; nothing else is wrong
+ * with the device, the batch can be run again), the ray statuses of
+ * swkb_propagate (message prefixed with the request index), SWKB_ERR_CUDA.
+ */
+swkb_status swkb_batch_run(swkb_batch* batch, const double* u_in, double* u_out,
+                           int32_t on_device);
+
+swkb_status swkb_batch_get_info(const swkb_batch* batch, swkb_batch_info* info);
+void swkb_batch_destroy(swkb_batch* batch);
+
+/* ---------------------------------------------------------------------------
  * Separation-of-variables reference (Sec. 3.1).  For a permittivity that
  * does not depend on x, the exact one-way field is u(x, z) = sum_i a_i
  * exp(i alpha_i x) phi_i(z) (Eq. series_sol), with (phi_i, alpha_i^2) the

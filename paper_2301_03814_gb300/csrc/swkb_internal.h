@@ -18,6 +18,9 @@ enum : unsigned {
   ST_BOUNDS = 16u,   // bounds-checked builds: a device index left its buffer
 };
 
+// Columns n2 of the DFT's pass 1 handled by one block.
+constexpr int FFT1_COLS = 8;
+
 template <typename T> struct C2;
 template <> struct C2<float> { using type = float2; };
 template <> struct C2<double> { using type = double2; };
@@ -155,8 +158,49 @@ template <typename T> size_t resum_smem_bytes(int wcap, int tile_points);
 template <typename T> cudaError_t prepare_kernels(int resum_smem);
 // Message returned by swkb_last_error() on this thread.
 void set_last_error(const char* msg);
+// swkb_status of a kernel status word (ST_* bits; SWKB_OK for 0), setting
+// the thread's last-error message.
+swkb_status status_from_bits(unsigned bits);
 // Raise only the FFT kernel's shared-memory limit on the current device.
 template <typename T> cudaError_t prepare_fft_kernels();
+
+// What the persistent batch kernel (swkb_batch.cu) takes from a plan: sizes,
+// the plan's own buffers and ray-buffer sets, and the argument blocks of its
+// screen steps (built exactly as the plan's own launches build them).
+template <typename T>
+struct PlanParts {
+  int N, n_z, M, Mr, NRT, Nt, n_max, mirror, sym, N1, n_cols, pieces;
+  int stage_rows, stage_stride;      // RK4 stage rows (screens q >= rows - 1 share the last)
+  int march_bx, march_blocks;        // FP64: ceil(Mr / 32) x ceil(NRT / 8) blocks of (32, 8);
+                                     // FP32: ceil(Mr ceil(NRT / 2) / 256) blocks of 256
+  int bracket_bx;                    // bracket blocks of 256 threads along the modes
+  int resum_blocks, resum_pw;        // resummation blocks (tiles x mode groups), points per lane
+  size_t resum_smem;                 // shared memory of one resummation block
+  int fft1_blocks, fft2_blocks;      // pass-1 blocks (N2 / FFT1_COLS), pass-2 blocks (modes formed)
+  size_t fft1_smem;
+  int reduce_n;                      // threads of the final reduction
+  int out_off;                       // first physical point in the period
+  size_t rays, jlo_n;                // values per ray array / per bracket table
+  int sets;                          // ray-buffer sets the plan holds (1 or 2)
+  T* rd[2];
+  T* rph[2];
+  T* ra[2];
+  int* jlo[2];
+  int* jneg[2];
+  typename C2<T>::type* u;
+  unsigned* status;
+  FftArgs<T> fft_fresh;              // first screen: the DFT reads u
+  FftArgs<T> fft_next;               // later screens: pass 1 forms u from the partials
+  ReduceArgs<T> fin;                 // final reduction (projection, absorber) into u
+  MarchArgs<T> march;                // screen 0's stage row, ray set 0
+  BracketArgs<T> bracket;            // ray set 0
+  ResumArgs<T> resum;                // ray set 0
+};
+// Fails (SWKB_ERR_INVALID_ARG) for plans the batch kernel does not run:
+// inner planes, reused rays, or a one-pass DFT (fft_n1 = 1).
+template <typename T> swkb_status plan_parts(swkb_plan* p, PlanParts<T>* out);
+// Shared-memory bytes of one pass-1 DFT block for split N1.
+template <typename T> size_t fft1_smem_bytes(int N1);
 
 // Plan-level hooks used by the request server (swkb_server.cu).
 cudaStream_t plan_stream(swkb_plan* p);

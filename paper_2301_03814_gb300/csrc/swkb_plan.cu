@@ -216,7 +216,9 @@ swkb_status upload(swkb_plan* p, void** dst, const std::vector<double>& v) {
   return SWKB_OK;
 }
 
-swkb_status status_from_bits(unsigned bits) {
+}  // namespace
+
+swkb_status swkb::status_from_bits(unsigned bits) {
   if (bits & ST_BOUNDS)
     return fail(SWKB_ERR_CUDA, "a device index left its buffer (bounds-checked build)");
   if (bits & ST_CAUSTIC)
@@ -228,6 +230,8 @@ swkb_status status_from_bits(unsigned bits) {
   if (bits & ST_COVER) return fail(SWKB_ERR_RANGE, "ghost rays do not cover the screen");
   return SWKB_OK;
 }
+
+namespace {
 
 // Intervals of the FP32 medium table of one column (layout in swkb_internal.h).
 int table32_intervals(const swkb_plan* p) { return (p->mirror ? 2 : 1) * p->n_int + 1; }
@@ -668,6 +672,22 @@ ResumArgs<T> resum_args(const swkb_plan* p, const T* d, const T* ph, const T* a,
   ra.modes_per_group = p->modes_per_group; ra.n_max = p->n_max; ra.wcap = p->wcap;
   ra.part = (V*)p->part; ra.status = p->status;
   return ra;
+}
+
+template <typename T>
+FftArgs<T> fft_args(const swkb_plan* p, bool fuse) {
+  using V = typename C2<T>::type;
+  FftArgs<T> f;
+  f.u = (const V*)p->u; f.tw = (const V*)p->tw; f.Y = (V*)p->Y;
+  f.N = p->N; f.N1 = p->N1; f.N2 = p->N2; f.log2N2 = p->log2N2; f.n_max = p->n_max;
+  f.mirror = p->mirror;
+  f.part = fuse ? (const V*)p->part : nullptr;
+  f.n_part = p->n_groups;
+  f.sym = p->sym;
+  f.W = (const T*)p->W;
+  f.inv_N = (T)(1.0 / p->N);
+  f.ephi = (const V*)p->ephi_d; f.c = (V*)p->c;
+  return f;
 }
 
 template <typename T>
@@ -1517,6 +1537,59 @@ swkb_status autotune_plan(swkb_plan* p) {
 }  // namespace
 
 namespace swkb {
+
+template <typename T>
+swkb_status plan_parts(swkb_plan* p, PlanParts<T>* o) {
+  using V = typename C2<T>::type;
+  if ((p->precision == SWKB_FP64) != (sizeof(T) == 8))
+    return fail(SWKB_ERR_INVALID_ARG, "plan precision does not match the batch");
+  if (p->planes > 1 || p->reuse_rays)
+    return fail(SWKB_ERR_INVALID_ARG, "batched plans march every screen and have no inner planes");
+  if (p->N1 < 2)
+    return fail(SWKB_ERR_INVALID_ARG, "batched plans need a two-pass DFT (fft_n1 >= 2)");
+  *o = PlanParts<T>{};
+  o->N = p->N; o->n_z = p->n_z; o->M = p->M; o->Mr = p->Mr; o->NRT = p->NRT; o->Nt = p->Nt;
+  o->n_max = p->n_max; o->mirror = p->mirror; o->sym = p->sym; o->N1 = p->N1;
+  o->n_cols = p->n_cols; o->pieces = p->pieces;
+  o->stage_rows = p->stage_rows;
+  o->stage_stride = 2 * p->Nt + 1;
+  if (sizeof(T) == 8) {
+    o->march_bx = (p->Mr + 31) / 32;
+    o->march_blocks = o->march_bx * ((p->NRT + 7) / 8);
+  } else {
+    o->march_bx = 0;
+    o->march_blocks = (int)(((long long)p->Mr * ((p->NRT + 1) / 2) + 255) / 256);
+  }
+  o->bracket_bx = (p->Mr + 255) / 256;
+  o->resum_blocks = p->n_tiles_run * p->n_groups;
+  o->resum_pw = p->PW;
+  o->resum_smem = resum_smem_bytes<T>(p->wcap, p->TM);
+  o->fft1_blocks = p->N2 / FFT1_COLS;
+  o->fft2_blocks = p->mirror ? p->n_max + 1 : p->M;
+  o->fft1_smem = fft1_smem_bytes<T>(p->N1);
+  o->reduce_n = (p->mirror || p->sym) ? p->N / 2 + 1 : p->N;
+  o->out_off = p->mirror ? p->n_z : 0;
+  o->rays = (size_t)p->NRT * p->Mr;
+  o->jlo_n = (size_t)(p->alloc_tiles + 1) * p->Mr;
+  o->sets = p->overlap ? 2 : 1;
+  o->rd[0] = (T*)p->rd; o->rph[0] = (T*)p->rph; o->ra[0] = (T*)p->ra;
+  o->jlo[0] = p->jlo; o->jneg[0] = p->jlo_neg;
+  o->rd[1] = (T*)p->rd1; o->rph[1] = (T*)p->rph1; o->ra[1] = (T*)p->ra1;
+  o->jlo[1] = p->jlo1; o->jneg[1] = p->jlo_neg1;
+  o->u = (V*)p->u;
+  o->status = p->status;
+  o->fft_fresh = fft_args<T>(p, false);
+  o->fft_next = fft_args<T>(p, true);
+  o->fin = ReduceArgs<T>{(const V*)p->part, p->n_groups, p->N, (const T*)p->W, p->mirror, p->sym,
+                         (V*)p->u};
+  o->march = march_args<T>(p, 0);
+  o->bracket = bracket_args<T>(p, (const T*)p->rd);
+  o->resum = resum_args<T>(p, (const T*)p->rd, (const T*)p->rph, (const T*)p->ra,
+                           (const V*)p->c);
+  return SWKB_OK;
+}
+template swkb_status plan_parts<float>(swkb_plan*, PlanParts<float>*);
+template swkb_status plan_parts<double>(swkb_plan*, PlanParts<double>*);
 
 cudaStream_t plan_stream(swkb_plan* p) { return p->stream; }
 size_t plan_bytes(const swkb_plan* p) { return p->bytes; }

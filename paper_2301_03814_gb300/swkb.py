@@ -39,7 +39,8 @@ EXPORTED = ("swkb_options_default", "swkb_plan_create", "swkb_plan_get_info", "s
             "swkb_plan_get_stats", "swkb_server_create", "swkb_submit",
             "swkb_poll", "swkb_cancel", "swkb_server_get_stats", "swkb_server_destroy",
             "swkb_last_error", "swkb_status_string", "swkb_modes_noalloc", "swkb_sym_eig",
-            "swkb_hill_propagate")
+            "swkb_hill_propagate", "swkb_batch_options_default", "swkb_batch_create",
+            "swkb_batch_run", "swkb_batch_get_info", "swkb_batch_destroy")
 
 
 class SwkbError(RuntimeError):
@@ -94,6 +95,18 @@ class swkb_request(ctypes.Structure):
                 ("n_screens", c_int32)]
 
 
+class swkb_batch_options(ctypes.Structure):
+    _fields_ = [("ctas_per_sm", c_int32), ("wait_limit_ms", c_int32), ("device", c_int32),
+                ("cuda_stream", c_void_p)]
+
+
+class swkb_batch_info(ctypes.Structure):
+    _fields_ = [("instances", c_int32), ("precision", c_int32), ("grid", c_int32),
+                ("ctas_per_sm", c_int32), ("threads", c_int32), ("jobs", c_int32),
+                ("items", ctypes.c_int64), ("steps", c_int32), ("shared_bytes", c_size_t),
+                ("device_bytes", c_size_t)]
+
+
 class swkb_server_stats(ctypes.Structure):
     _fields_ = [("submitted", c_uint64), ("completed", c_uint64), ("failed", c_uint64),
                 ("rejected", c_uint64), ("resident", c_int32), ("queued", c_int32),
@@ -144,6 +157,17 @@ def lib():
                                           c_void_p, c_int32, c_void_p, c_void_p, c_void_p,
                                           c_int32, c_void_p]
         L.swkb_hill_propagate.restype = c_int32
+        L.swkb_batch_options_default.argtypes = [POINTER(swkb_batch_options)]
+        L.swkb_batch_options_default.restype = None
+        L.swkb_batch_create.argtypes = [c_int32, POINTER(swkb_request), POINTER(swkb_batch_options),
+                                        POINTER(c_void_p)]
+        L.swkb_batch_create.restype = c_int32
+        L.swkb_batch_run.argtypes = [c_void_p, c_void_p, c_void_p, c_int32]
+        L.swkb_batch_run.restype = c_int32
+        L.swkb_batch_get_info.argtypes = [c_void_p, POINTER(swkb_batch_info)]
+        L.swkb_batch_get_info.restype = c_int32
+        L.swkb_batch_destroy.argtypes = [c_void_p]
+        L.swkb_batch_destroy.restype = None
         L.swkb_last_error.restype = c_char_p
         L.swkb_status_string.restype = c_char_p
         L.swkb_status_string.argtypes = [c_int32]
@@ -460,6 +484,70 @@ class Server:
             self.close()
         except Exception:
             pass
+def _request(problem, opt: swkb_options, keep: _Keep, u0=None, q0=0, n_screens=None):
+    """swkb_request for a workloads.Problem (the buffers stay alive in keep)."""
+    prof = make_profile(problem.profile, keep)
+    dom = swkb_domain(problem.z_a, problem.z_b, problem.x0, problem.bc)
+    u = np.ascontiguousarray(problem.u0 if u0 is None else u0, dtype=np.complex128)
+    keep.refs.extend([prof, dom, opt, u])
+    return swkb_request(ctypes.pointer(prof), float(problem.k), ctypes.pointer(dom),
+                        int(problem.n_z), float(problem.dx), ctypes.pointer(opt),
+                        u.ctypes.data_as(POINTER(c_double)), int(q0),
+                        int(problem.n_screens if n_screens is None else n_screens))
+
+
+class Batch:
+    """Many problems advanced in one persistent launch (swkb_batch_*).
+    problems: workloads.Problem list (each runs its own n_screens from its
+    u0); precision shared by all; autotune / tiling as for Plan."""
+
+    def __init__(self, problems, precision=SWKB_MIXED, ctas_per_sm=0, wait_limit_ms=0,
+                 device=0, stream=None, autotune=False, tiling=None):
+        keep = _Keep()
+        n = len(problems)
+        reqs = (swkb_request * n)()
+        for i, pb in enumerate(problems):
+            opt = options_for(pb, precision, None, device, autotune, False, 0, tiling)
+            reqs[i] = _request(pb, opt, keep)
+        bo = swkb_batch_options(int(ctas_per_sm), int(wait_limit_ms), int(device), stream)
+        self.handle = c_void_p()
+        check(lib().swkb_batch_create(n, reqs, byref(bo), byref(self.handle)))
+        self.n_z = [int(pb.n_z) for pb in problems]
+        self.offsets = np.concatenate([[0], np.cumsum(self.n_z)]).astype(np.int64)
+        self.total = int(self.offsets[-1])
+        self.info = swkb_batch_info()
+        check(lib().swkb_batch_get_info(self.handle, byref(self.info)))
+
+    def run(self, u_in=None):
+        """Host arrays: returns the list of output fields (complex128)."""
+        out = np.empty(self.total, np.complex128)
+        src = None
+        if u_in is not None:
+            src = np.ascontiguousarray(np.concatenate(u_in), dtype=np.complex128)
+        check(lib().swkb_batch_run(self.handle, None if src is None else src.ctypes.data,
+                                   out.ctypes.data, 0))
+        return [out[self.offsets[i]:self.offsets[i + 1]] for i in range(len(self.n_z))]
+
+    def run_status(self):
+        """Runs without reading the outputs; returns the status (no raise)."""
+        return lib().swkb_batch_run(self.handle, None, None, 0)
+
+    def run_device(self, in_ptr, out_ptr):
+        """Device pointers (concatenated complex128 fields; in_ptr may be None)."""
+        return check(lib().swkb_batch_run(self.handle, in_ptr, out_ptr, 1))
+
+    def close(self):
+        if self.handle:
+            lib().swkb_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Plan:
     """A plan for one workloads.Problem (or equivalent fields)."""
 

@@ -48,7 +48,8 @@ def test_status_strings_and_defaults(built):
 
 
 STRUCTS = ("swkb_profile", "swkb_domain", "swkb_options", "swkb_plan_info", "swkb_plan_stats",
-           "swkb_request", "swkb_server_stats", "swkb_hill_desc")
+           "swkb_request", "swkb_server_stats", "swkb_hill_desc", "swkb_batch_options",
+           "swkb_batch_info")
 
 
 def test_struct_layouts_match_header(tmp_path):
