@@ -819,7 +819,19 @@ __device__ __forceinline__ void resum_body(const ResumArgs<T>& p, int blk, int t
     const int W = jh - jl + 4;
     const int base = mirrored ? p.N - m0 - (p.NRT - jb - p.G) * p.R : (jb - p.G) * p.R - m0;
     const T dsign = mirrored ? T(-1) : T(1);
-    const V cn = ld<LDC>(p.c + i);
+    // FP32: the mode coefficient enters as |c_n| (scaling the amplitudes) and
+    // arg(c_n) / 2 pi (added to the phases, in turns) -- cpol, formed by the
+    // DFT -- so that each term is |c_n| a e^{2 pi i t}: two FMAs instead of a
+    // complex product.  FP64 multiplies by c_n.
+    V cn;
+    T cmag = T(1), carg = T(0);
+    if constexpr (sizeof(T) == 4) {
+      const V cp = ld<LDC>(p.cpol + i);
+      cmag = cp.x;
+      carg = cp.y;
+    } else {
+      cn = ld<LDC>(p.c + i);
+    }
     const unsigned nn = (unsigned)(i - p.n_max);
     __syncwarp();
     if (ok) {
@@ -828,16 +840,26 @@ __device__ __forceinline__ void resum_body(const ResumArgs<T>& p, int blk, int t
         const int w = lane + 32 * r;
         if (w < W) {
           s_X[w] = T(base + w * p.R) + dsign * rd[r];
-          s_ph[w] = rph[r];
-          s_a[w] = ra[r];
+          if constexpr (sizeof(T) == 4) {
+            s_ph[w] = rph[r] + carg;
+            s_a[w] = ra[r] * cmag;
+          } else {
+            s_ph[w] = rph[r];
+            s_a[w] = ra[r];
+          }
         }
       }
       for (int w = lane + 32 * PF; w < W; w += 32) {   // beyond the prefetched rounds
         const long long o = bchk((long long)ray_of(mirrored, jb, w) * p.Mr + col,
                                  (long long)p.NRT * p.Mr, st);
         s_X[w] = T(base + w * p.R) + dsign * ld<LD>(p.d + o);
-        s_ph[w] = ld<LD>(p.ph + o);
-        s_a[w] = ld<LD>(p.a + o);
+        if constexpr (sizeof(T) == 4) {
+          s_ph[w] = ld<LD>(p.ph + o) + carg;
+          s_a[w] = ld<LD>(p.a + o) * cmag;
+        } else {
+          s_ph[w] = ld<LD>(p.ph + o);
+          s_a[w] = ld<LD>(p.a + o);
+        }
       }
     }
     // issue the next mode's window and the following mode's brackets
@@ -858,6 +880,7 @@ __device__ __forceinline__ void resum_body(const ResumArgs<T>& p, int blk, int t
                     h21, h10, b0, b1, b2, b3);
       cubic_through(s_a[w - 1], s_a[w], s_a[w + 1], s_a[w + 2], r21, r10, r32, r20, r31, r30,
                     h21, h10, a0, a1, a2, a3);
+      if constexpr (sizeof(T) == 4) b0 = minus_rint(b0);   // whole turns do not matter
       store_cf(s_cf + RESUM_CF * w, X1, X2, b0, b1, b2, b3, a0, a1, a2, a3);
     }
     __syncwarp();
@@ -875,24 +898,53 @@ __device__ __forceinline__ void resum_body(const ResumArgs<T>& p, int blk, int t
     while (w < W - 3 && s_X[w + 1] <= xv0) ++w;
     T X1, X2, b0, b1, b2, b3, a0, a1, a2, a3;
     load_cf<T>(s_cf + RESUM_CF * w, X1, X2, b0, b1, b2, b3, a0, a1, a2, a3);
-    unsigned nm = (nn * (unsigned)(m0 + x0)) & mask;
+    if constexpr (sizeof(T) == 4) {
+      // The exact integer phase n m / N mod 1 of the run's middle point,
+      // moved into [-1/2, 1/2); the run's points differ from it by
+      // (q - PW/2) n / N, exact in FP32 (multiples of 1/N below 2^(24 - log2 N)),
+      // so each point's turn count costs one FMA.  The phase cubic is reduced
+      // to (-1/2, 1/2] at its interval start, so the argument of the sine
+      // stays within a few turns.
+      const unsigned nmc = (nn * (unsigned)(m0 + x0 + PW / 2)) & mask;
+      T bc = exact_u2f(nmc, T()) * invN;
+      bc = bc >= T(0.5) ? bc - T(1) : bc;
+      const T nN = T((int)nn) * invN;
 #pragma unroll
-    for (int q = 0; q < PW; ++q) {
-      const T xv = xv0 + T(q);   // exact
-      while (w < W - 3 && X2 <= xv) {
-        ++w;
-        load_cf<T>(s_cf + RESUM_CF * w, X1, X2, b0, b1, b2, b3, a0, a1, a2, a3);
+      for (int q = 0; q < PW; ++q) {
+        const T xv = xv0 + T(q);   // exact
+        while (w < W - 3 && X2 <= xv) {
+          ++w;
+          load_cf<T>(s_cf + RESUM_CF * w, X1, X2, b0, b1, b2, b3, a0, a1, a2, a3);
+        }
+        const T tau = xv - X1;
+        const T phv = ((b3 * tau + b2) * tau + b1) * tau + b0;
+        const T av = ((a3 * tau + a2) * tau + a1) * tau + a0;
+        const T t = fmaf(T(q - PW / 2), nN, bc) + phv;
+        T sn, cs;
+        sincos_turns(t, &sn, &cs);
+        accr[q] = fmaf(av, cs, accr[q]);
+        acci[q] = fmaf(av, sn, acci[q]);
       }
-      const T tau = xv - X1;
-      const T phv = ((b3 * tau + b2) * tau + b1) * tau + b0;
-      const T av = ((a3 * tau + a2) * tau + a1) * tau + a0;
-      const T t = minus_rint(exact_u2f(nm, T()) * invN + phv);
-      T sn, cs;
-      sincos_turns(t, &sn, &cs);
-      const T ar = av * cn.x, ai = av * cn.y;
-      accr[q] += ar * cs - ai * sn;
-      acci[q] += ar * sn + ai * cs;
-      nm = (nm + nn) & mask;
+    } else {
+      unsigned nm = (nn * (unsigned)(m0 + x0)) & mask;
+#pragma unroll
+      for (int q = 0; q < PW; ++q) {
+        const T xv = xv0 + T(q);   // exact
+        while (w < W - 3 && X2 <= xv) {
+          ++w;
+          load_cf<T>(s_cf + RESUM_CF * w, X1, X2, b0, b1, b2, b3, a0, a1, a2, a3);
+        }
+        const T tau = xv - X1;
+        const T phv = ((b3 * tau + b2) * tau + b1) * tau + b0;
+        const T av = ((a3 * tau + a2) * tau + a1) * tau + a0;
+        const T t = minus_rint(exact_u2f(nm, T()) * invN + phv);
+        T sn, cs;
+        sincos_turns(t, &sn, &cs);
+        const T ar = av * cn.x, ai = av * cn.y;
+        accr[q] += ar * cs - ai * sn;
+        acci[q] += ar * sn + ai * cs;
+        nm = (nm + nn) & mask;
+      }
     }
   }
   // fixed-order sum of the warps' partial sums
@@ -1048,6 +1100,15 @@ __device__ __forceinline__ typename C2<T>::type cmul(typename C2<T>::type a,
 // w_{N1}^{n1 k1} for all k1.  N1 <= 64.
 // FFT1_COLS (columns per pass-1 block) is in swkb_internal.h
 
+// (|v|, arg(v) / 2 pi) of a complex value, the angle in turns in [-1/2, 1/2].
+template <typename T>
+__device__ __forceinline__ typename C2<T>::type polar_turns(typename C2<T>::type v) {
+  typename C2<T>::type r;
+  r.x = sqrt(v.x * v.x + v.y * v.y);
+  r.y = atan2(v.y, v.x) * T(0.15915494309189533577);
+  return r;
+}
+
 // Field value at grid point m formed from the resummation partials: the sum
 // over mode groups times the absorber, with the reflection of grounded plans
 // (same arithmetic as k_reduce).
@@ -1118,13 +1179,18 @@ __global__ void __launch_bounds__(256) k_fft1(const FftArgs<T> p) {
   fft1_body<T, LD_PLAIN>(p, blockIdx.x, threadIdx.x, smem_raw);
 }
 
-// out_i = c_i f_i (mode coefficients of a plane between screens).
+// out_i = c_i f_i (mode coefficients of a plane between screens), and its
+// polar form when pol is given.
 template <typename T>
 __global__ void k_cscale(const typename C2<T>::type* __restrict__ c,
                          const typename C2<T>::type* __restrict__ f,
-                         typename C2<T>::type* __restrict__ out, int M) {
+                         typename C2<T>::type* __restrict__ out,
+                         typename C2<T>::type* __restrict__ pol, int M) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < M) out[i] = cmul<T>(c[i], f[i]);
+  if (i >= M) return;
+  const typename C2<T>::type v = cmul<T>(c[i], f[i]);
+  out[i] = v;
+  if (pol) pol[i] = polar_turns<T>(v);
 }
 
 // w_{N2}^{idx} from the table of w_N (w_{N2} = w_N^{N1}).
@@ -1196,6 +1262,14 @@ __device__ __forceinline__ void fft2_body(const FftArgs<T>& p, int blk, int tid,
       V cm;
       cm.x = T(p.mirror) * cv.x; cm.y = T(p.mirror) * cv.y;
       p.c[2 * p.n_max - i] = cm;
+    }
+    if (p.cpol) {   // |c_n| and arg(c_n) / 2 pi (turns, in (-1/2, 1/2])
+      V pol = polar_turns<T>(cv);
+      p.cpol[i] = pol;
+      if (p.mirror && n > 0) {
+        if (p.mirror < 0) pol.y = pol.y > T(0) ? pol.y - T(0.5) : pol.y + T(0.5);
+        p.cpol[2 * p.n_max - i] = pol;
+      }
     }
   }
 }

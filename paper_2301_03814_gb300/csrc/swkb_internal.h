@@ -102,6 +102,7 @@ struct ResumArgs {
   const int* jlo;
   const int* jlo_neg;
   const typename C2<T>::type* c;   // [M] mode coefficients, range phase folded in
+  const typename C2<T>::type* cpol; // [M] FP32: (|c_n|, arg(c_n) / 2 pi), read instead of c
   int M, Mr, NRT, G, R, N, TM, PW, n_tiles, n_groups, modes_per_group, n_max, wcap;
   int sym;          // grounded: modes n < 0 are mirror images of -n; only the
                     // tiles of the physical half and tile 0 are summed
@@ -135,6 +136,7 @@ struct FftArgs {
   T inv_N;
   const typename C2<T>::type* ephi;  // [M] exp(i Phi_n)
   typename C2<T>::type* c;           // [M]
+  typename C2<T>::type* cpol;        // [M] (|c_n|, arg(c_n) / 2 pi), or nullptr
 };
 
 // launchers (defined in swkb_kernels.cu for T = float, double)
@@ -150,7 +152,8 @@ template <typename T> cudaError_t launch_output(const typename C2<T>::type* u, i
                                                 double* out, cudaStream_t s);
 template <typename T> cudaError_t launch_cscale(const typename C2<T>::type* c,
                                                 const typename C2<T>::type* f,
-                                                typename C2<T>::type* out, int M,
+                                                typename C2<T>::type* out,
+                                                typename C2<T>::type* pol, int M,
                                                 cudaStream_t s);
 template <typename T> size_t resum_smem_bytes(int wcap, int tile_points);
 // Raise the dynamic shared-memory limit of the resummation kernels

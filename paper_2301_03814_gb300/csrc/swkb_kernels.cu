@@ -162,8 +162,9 @@ cudaError_t prepare_fft_kernels() {
 
 template <typename T>
 cudaError_t launch_cscale(const typename C2<T>::type* c, const typename C2<T>::type* f,
-                          typename C2<T>::type* out, int M, cudaStream_t s) {
-  return launch_k(k_cscale<T>, dim3((M + 255) / 256), dim3(256), 0, s, c, f, out, M);
+                          typename C2<T>::type* out, typename C2<T>::type* pol, int M,
+                          cudaStream_t s) {
+  return launch_k(k_cscale<T>, dim3((M + 255) / 256), dim3(256), 0, s, c, f, out, pol, M);
 }
 
 template <typename T>
@@ -181,7 +182,7 @@ cudaError_t launch_output(const typename C2<T>::type* u, int offset, int n, doub
   template cudaError_t launch_resum<T>(const ResumArgs<T>&, cudaStream_t);                      \
   template cudaError_t launch_output<T>(const C2<T>::type*, int, int, double*, cudaStream_t);   \
   template cudaError_t launch_cscale<T>(const C2<T>::type*, const C2<T>::type*, C2<T>::type*,   \
-                                        int, cudaStream_t);                                     \
+                                        C2<T>::type*, int, cudaStream_t);                       \
   template size_t resum_smem_bytes<T>(int, int);                                                \
   template size_t fft1_smem_bytes<T>(int);                                                      \
   template cudaError_t prepare_kernels<T>(int);                                                 \

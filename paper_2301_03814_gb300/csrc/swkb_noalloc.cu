@@ -132,6 +132,7 @@ extern "C" swkb_status swkb_modes_noalloc(const double* u, int32_t n_fft, int32_
   f.inv_N = 1.0 / n_fft;
   f.ephi = d->unit_phase;
   f.c = reinterpret_cast<double2*>(c);
+  f.cpol = nullptr;
   e = swkb::launch_fft<double>(f, s);
   if (e != cudaSuccess) return err(SWKB_ERR_CUDA, cudaGetErrorString(e));
   return SWKB_OK;

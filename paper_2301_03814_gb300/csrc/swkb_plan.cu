@@ -112,6 +112,7 @@ struct swkb_plan {
   void* part = nullptr;
   void* Y = nullptr;
   void* c = nullptr;
+  void* cpol = nullptr;   // FP32: (|c_n|, arg(c_n) / 2 pi) of c
   void* rd = nullptr;
   void* rph = nullptr;
   void* ra = nullptr;
@@ -122,6 +123,7 @@ struct swkb_plan {
   void* pl_ph = nullptr;
   void* pl_a = nullptr;
   void* c_plane = nullptr;
+  void* cpol_plane = nullptr;
   void* ephi_pl = nullptr;
   int* jlo = nullptr;
   int* jlo_neg = nullptr;
@@ -500,6 +502,7 @@ swkb_status build_device(swkb_plan* p, const swkb_profile* prof) {
   TRY(dev_alloc(p, &p->part, (size_t)p->alloc_groups * N * sizeof(V)));
   TRY(dev_alloc(p, &p->Y, (size_t)N * sizeof(V)));
   TRY(dev_alloc(p, &p->c, (size_t)M * sizeof(V)));
+  if (sizeof(T) == 4) TRY(dev_alloc(p, &p->cpol, (size_t)M * sizeof(V)));
   const size_t rays = (size_t)p->NRT * p->Mr;
   TRY(dev_alloc(p, &p->rd, rays * sizeof(T)));
   TRY(dev_alloc(p, &p->rph, rays * sizeof(T)));
@@ -510,6 +513,7 @@ swkb_status build_device(swkb_plan* p, const swkb_profile* prof) {
     TRY(dev_alloc(p, &p->pl_ph, pr * sizeof(T)));
     TRY(dev_alloc(p, &p->pl_a, pr * sizeof(T)));
     TRY(dev_alloc(p, &p->c_plane, (size_t)M * sizeof(V)));
+    if (sizeof(T) == 4) TRY(dev_alloc(p, &p->cpol_plane, (size_t)M * sizeof(V)));
     TRY(dev_alloc(p, &p->ephi_pl, (size_t)(p->planes - 1) * M * sizeof(V)));
   }
   const size_t jn = (size_t)(p->alloc_tiles + 1) * p->Mr;
@@ -666,6 +670,7 @@ ResumArgs<T> resum_args(const swkb_plan* p, const T* d, const T* ph, const T* a,
   ra.d = d; ra.ph = ph; ra.a = a; ra.jlo = jlo ? jlo : p->jlo;
   ra.jlo_neg = jlo ? jlo_neg : p->jlo_neg;
   ra.c = c;
+  ra.cpol = (c == (const typename C2<T>::type*)p->c) ? (const V*)p->cpol : (const V*)p->cpol_plane;
   ra.M = p->M; ra.Mr = p->Mr; ra.sym = p->sym; ra.n_tiles_run = p->n_tiles_run; ra.NRT = p->NRT;
   ra.G = p->G; ra.R = p->R; ra.N = p->N; ra.TM = p->TM;
   ra.PW = p->PW; ra.n_tiles = p->n_tiles; ra.n_groups = p->n_groups;
@@ -686,7 +691,7 @@ FftArgs<T> fft_args(const swkb_plan* p, bool fuse) {
   f.sym = p->sym;
   f.W = (const T*)p->W;
   f.inv_N = (T)(1.0 / p->N);
-  f.ephi = (const V*)p->ephi_d; f.c = (V*)p->c;
+  f.ephi = (const V*)p->ephi_d; f.c = (V*)p->c; f.cpol = (V*)p->cpol;
   return f;
 }
 
@@ -711,7 +716,7 @@ swkb_status launch_screen(swkb_plan* p, int q, bool u_fresh) {
   f.sym = p->sym;
   f.W = (const T*)p->W;
   f.inv_N = (T)(1.0 / p->N);
-  f.ephi = (const V*)p->ephi_d; f.c = (V*)p->c;
+  f.ephi = (const V*)p->ephi_d; f.c = (V*)p->c; f.cpol = (V*)p->cpol;
   TRY(timed(p, SWKB_KERNEL_FFT, p->N1 > 1 ? 2 : 1, [&] { return launch_fft<T>(f, s); }));
   const MarchArgs<T> ma = march_args<T>(p, q);
   const bool multi = p->n_cols > 1;
@@ -829,7 +834,7 @@ swkb_status overlapped_screen(swkb_plan* p, int q, int b, bool fresh) {
   f.sym = p->sym;
   f.W = (const T*)p->W;
   f.inv_N = (T)(1.0 / p->N);
-  f.ephi = (const V*)p->ephi_d; f.c = (V*)p->c;
+  f.ephi = (const V*)p->ephi_d; f.c = (V*)p->c; f.cpol = (V*)p->cpol;
   TRY(timed(p, SWKB_KERNEL_FFT, p->N1 > 1 ? 2 : 1, [&] { return launch_fft<T>(f, s); }));
   // brackets and sum of screen q, once its rays are there (the ray stream
   // goes on with the next march)
@@ -936,7 +941,7 @@ swkb_status enqueue_planes(swkb_plan* p, const double* u0, int q0, int n, int P,
     f.sym = p->sym;
     f.W = (const T*)p->W;
     f.inv_N = (T)(1.0 / p->N);
-    f.ephi = (const V*)p->ephi_d; f.c = (V*)p->c;
+    f.ephi = (const V*)p->ephi_d; f.c = (V*)p->c; f.cpol = (V*)p->cpol;
     TRY(timed(p, SWKB_KERNEL_FFT, p->N1 > 1 ? 2 : 1, [&] { return launch_fft<T>(f, s); }));
     MarchArgs<T> ma = march_args<T>(p, q);
     if (P > 1) {
@@ -952,7 +957,7 @@ swkb_status enqueue_planes(swkb_plan* p, const double* u0, int q0, int n, int P,
       // c_n of plane j: the screen's c_n (carried over dx) times exp(i k (j/P - 1) dx P_bar_n)
       const V* fj = (const V*)p->ephi_pl + (size_t)(j - 1) * p->M;
       TRY(timed(p, SWKB_KERNEL_REDUCE, 1, [&] {
-        return launch_cscale<T>((const V*)p->c, fj, (V*)p->c_plane, p->M, s);
+        return launch_cscale<T>((const V*)p->c, fj, (V*)p->c_plane, (V*)p->cpol_plane, p->M, s);
       }));
       const ResumArgs<T> ra = resum_args<T>(p, (const T*)p->pl_d + o, (const T*)p->pl_ph + o,
                                             (const T*)p->pl_a + o, (const V*)p->c_plane);
@@ -1407,10 +1412,11 @@ size_t device_bytes(const swkb_plan* p) {
   b += (size_t)p->N * V;                                            // twiddles
   if (p->absorber_frac > 0) b += (size_t)p->N * T;                  // absorber
   b += (size_t)p->N * V * (2 + (size_t)p->alloc_groups) + (size_t)p->M * V;  // u, Y, partials, c
+  if (T == 4) b += (size_t)p->M * V;                                 // polar c
   b += 3 * (size_t)p->NRT * p->Mr * T * (p->overlap ? 2 : 1);     // rays (one or two sets)
   if (p->planes > 1)                                                 // inner planes
     b += (size_t)(p->planes - 1) * (3 * (size_t)p->NRT * p->Mr * T + (size_t)p->M * V) +
-         (size_t)p->M * V;
+         (size_t)p->M * V * (T == 4 ? 2 : 1);
   b += (size_t)(p->alloc_tiles + 1) * p->Mr * sizeof(int) * (p->sym ? 2 : 1) *
        (p->overlap ? 2 : 1);
   b += 16 + 2 * (size_t)std::max(p->N, p->n_z) * sizeof(double);   // status, io

@@ -8,7 +8,7 @@ import pytest
 
 from paper_2301_03814_gb300 import swkb
 from paper_2301_03814_gb300 import workloads as w
-from oracle.swkb_oracle import Oracle, rel_l2
+from oracle.swkb_oracle import rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -51,14 +51,25 @@ def test_batch_fields_equal_plans_alone_bit_for_bit(prec):
     b.close()
 
 
+_oracle = {}
+
+
 @pytest.mark.parametrize("prec,tol", [(swkb.SWKB_FP64, 1e-9), (swkb.SWKB_MIXED, 1e-4)],
                          ids=["fp64", "mixed"])
 def test_batch_of_uneven_instances_matches_oracle(prec, tol):
+    from oracle.swkb_parallel import OraclePool, ParallelOracle
     c4 = w.batch_uneven(4, 64)
     pbs = [c4[i].with_(n_screens=2) for i in (0, 12, 33, 50)]
     got = swkb.Batch(pbs, prec).run()
-    for pb, g in zip(pbs, got):
-        assert rel_l2(g, Oracle(pb).propagate(pb.u0)) < tol
+    if "want" not in _oracle:
+        with OraclePool() as pool:
+            want = []
+            for pb in pbs:
+                with ParallelOracle(pb, pool=pool) as o:
+                    want.append(o.propagate(pb.u0))
+        _oracle["want"] = want
+    for g, ref in zip(got, _oracle["want"]):
+        assert rel_l2(g, ref) < tol
 
 
 def test_batch_new_inputs_and_device_buffers():
