@@ -23,9 +23,10 @@
 // set's last reader.  The other dependencies: FFT1(s) on RESUM(s - 1) (its
 // partial sums are the field) or INIT; FFT2(s) on FFT1(s); BRACKET(s) on
 // MARCH(s); RESUM(s) on FFT2(s) and BRACKET(s); REDUCE on the last RESUM;
-// OUTPUT on REDUCE.  Per instance and step kind a monotonic counter counts
-// finished items; a job waits until its producers' counters reach their
-// totals through that screen.
+// OUTPUT on REDUCE.  Monotonic counters per (instance, step kind, screen mod
+// 3) count finished items; a job waits until its producers' counters reach
+// their totals through that screen (screens sharing a counter are three
+// apart, and the dependencies above order them).
 //
 // Execution.  A CTA claims the next item (an atomic per job; a shared job
 // pointer advances past exhausted jobs), thread 0 waits for the item's
@@ -70,7 +71,7 @@ constexpr int VB_INIT = 8, VB_MARCH = 2, VB_FFT1 = 4, VB_FFT2 = 8, VB_BRACKET = 
 
 struct Job {
   int inst, phase, step, items;
-  int dep_c[2];          // counter index inst * PH_COUNT + phase, or -1
+  int dep_c[2];          // counter (inst * PH_COUNT + phase) * kSets + step mod kSets, or -1
   unsigned dep_need[2];  // finished items that counter must reach
 };
 
@@ -93,7 +94,7 @@ struct Ctl {
   const Job* jobs;
   int n_jobs;
   unsigned* claimed;               // [n_jobs] items handed out
-  unsigned* done;                  // [n_inst * PH_COUNT + 1] finished items (last: never)
+  unsigned* done;                  // [n_inst * PH_COUNT * kSets + 1] finished items (last: never)
   int* cur;                        // first job that may have unclaimed items
   unsigned* error;                 // 0, or 1: a wait gave up
   unsigned long long wait_ns;      // bound of every wait
@@ -314,7 +315,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 1)
     __syncthreads();
     if (tid == 0) {
       __threadfence();
-      atomicAdd(c.done + jb.inst * PH_COUNT + jb.phase, 1u);
+      atomicAdd(c.done + (jb.inst * PH_COUNT + jb.phase) * kSets + jb.step % kSets, 1u);
     }
   }
 }
@@ -483,10 +484,19 @@ swkb_status build(swkb_batch* b, const swkb_request* reqs, const swkb_batch_opti
     for (int i = 0; i < n; ++i)
       items[(size_t)i * PH_COUNT + PH_RESUM] = cdiv(hi[i].resum_blocks, b->resum_per_item);
   }
-  // the queue
-  const int never = n * PH_COUNT;   // a counter nothing increments
+  // the queue.  Finished items are counted per (instance, step kind, screen
+  // mod 3): two screens of one kind that share a counter are three apart,
+  // and the dependency chain keeps the later one from starting before the
+  // earlier one has finished (MARCH(s + 3) waits for RESUM(s), which waits for
+  // BRACKET(s) and FFT2(s), which wait for MARCH(s) and FFT1(s)), so a count
+  // on a counter always counts whole screens in order.  (One counter per
+  // kind would not: MARCH(s + 1) items may finish while MARCH(s) items run.)
+  const int never = n * PH_COUNT * kSets;   // a counter nothing increments
   std::vector<Job> jobs;
-  auto ctr = [](int i, int ph) { return i * PH_COUNT + ph; };
+  auto ctr = [](int i, int ph, int step) { return (i * PH_COUNT + ph) * kSets + step % kSets; };
+  auto it = [&](int i, int ph) { return (long long)items[(size_t)i * PH_COUNT + ph]; };
+  // items finished on the counter of screen s of kind ph once screen s is done
+  auto upto = [&](int i, int ph, int s) { return (long long)(s / kSets + 1) * it(i, ph); };
   auto push = [&](int i, int ph, int step, int c0 = -1, long long n0 = 0, int c1 = -1,
                   long long n1 = 0) {
     Job j;
@@ -495,7 +505,6 @@ swkb_status build(swkb_batch* b, const swkb_request* reqs, const swkb_batch_opti
     j.dep_c[1] = c1; j.dep_need[1] = (unsigned)n1;
     jobs.push_back(j);
   };
-  auto it = [&](int i, int ph) { return (long long)items[(size_t)i * PH_COUNT + ph]; };
   int smax = 0;
   for (int i = 0; i < n; ++i) smax = std::max(smax, b->n_screens[i]);
   for (int i = 0; i < n; ++i) push(i, PH_INIT, 0);
@@ -510,34 +519,37 @@ swkb_status build(swkb_batch* b, const swkb_request* reqs, const swkb_batch_opti
     for (int i = g; i < n; i += 3) {
       const int m = s + 1;   // march a screen ahead into set m mod 3
       if (m < b->n_screens[i]) {
-        if (m >= kSets) push(i, PH_MARCH, m, ctr(i, PH_RESUM), (m - kSets + 1) * it(i, PH_RESUM));
-        else push(i, PH_MARCH, m);
+        if (m >= kSets)   // the set's last reader, RESUM(m - 3), is done
+          push(i, PH_MARCH, m, ctr(i, PH_RESUM, m - kSets), upto(i, PH_RESUM, m - kSets));
+        else
+          push(i, PH_MARCH, m);
       }
     }
   };
   for (int s = 0; s <= smax; ++s) {
     for (int i = 0; i < n; ++i)   // reduced at the end of step s - 1
-      if (s == b->n_screens[i]) push(i, PH_OUTPUT, s, ctr(i, PH_REDUCE), it(i, PH_REDUCE));
+      if (s == b->n_screens[i])
+        push(i, PH_OUTPUT, s, ctr(i, PH_REDUCE, s - 1), it(i, PH_REDUCE));
     if (s == smax) break;
     for (int i = 0; i < n; ++i)
       if (s < b->n_screens[i]) {
-        if (s == 0) push(i, PH_FFT1, s, ctr(i, PH_INIT), it(i, PH_INIT));
-        else push(i, PH_FFT1, s, ctr(i, PH_RESUM), s * it(i, PH_RESUM));
+        if (s == 0) push(i, PH_FFT1, s, ctr(i, PH_INIT, 0), it(i, PH_INIT));
+        else push(i, PH_FFT1, s, ctr(i, PH_RESUM, s - 1), upto(i, PH_RESUM, s - 1));
       }
     march_group(s, 0);
     for (int i = 0; i < n; ++i)
-      if (s < b->n_screens[i]) push(i, PH_FFT2, s, ctr(i, PH_FFT1), (s + 1) * it(i, PH_FFT1));
+      if (s < b->n_screens[i]) push(i, PH_FFT2, s, ctr(i, PH_FFT1, s), upto(i, PH_FFT1, s));
     for (int i = 0; i < n; ++i)
-      if (s < b->n_screens[i]) push(i, PH_BRACKET, s, ctr(i, PH_MARCH), (s + 1) * it(i, PH_MARCH));
+      if (s < b->n_screens[i]) push(i, PH_BRACKET, s, ctr(i, PH_MARCH, s), upto(i, PH_MARCH, s));
     march_group(s, 1);
     for (int i = 0; i < n; ++i)
       if (s < b->n_screens[i])
-        push(i, PH_RESUM, s, ctr(i, PH_FFT2), (s + 1) * it(i, PH_FFT2), ctr(i, PH_BRACKET),
-             (s + 1) * it(i, PH_BRACKET));
+        push(i, PH_RESUM, s, ctr(i, PH_FFT2, s), upto(i, PH_FFT2, s), ctr(i, PH_BRACKET, s),
+             upto(i, PH_BRACKET, s));
     march_group(s, 2);
     for (int i = 0; i < n; ++i)
       if (s == b->n_screens[i] - 1)
-        push(i, PH_REDUCE, s, ctr(i, PH_RESUM), (s + 1) * it(i, PH_RESUM));
+        push(i, PH_REDUCE, s, ctr(i, PH_RESUM, s), upto(i, PH_RESUM, s));
   }
   // test hook: an item that waits on a counter nothing increments, so that
   // the bounded wait runs out (SWKB_BATCH_STALL=1)
@@ -561,7 +573,7 @@ swkb_status build(swkb_batch* b, const swkb_request* reqs, const swkb_batch_opti
   BCK(cudaMemcpyAsync(b->jobs, jobs.data(), sizeof(Job) * jobs.size(), cudaMemcpyHostToDevice,
                       b->stream));
   TRY_B(balloc(b, (void**)&b->claimed, sizeof(unsigned) * jobs.size()));
-  TRY_B(balloc(b, (void**)&b->done, sizeof(unsigned) * (n * PH_COUNT + 1)));
+  TRY_B(balloc(b, (void**)&b->done, sizeof(unsigned) * (n * PH_COUNT * kSets + 1)));
   TRY_B(balloc(b, (void**)&b->cur, sizeof(int)));
   TRY_B(balloc(b, (void**)&b->error, sizeof(unsigned)));
   // launch shape: as many co-resident CTAs as fit (or as asked)
@@ -596,7 +608,7 @@ swkb_status enqueue_run(swkb_batch* b) {
   c.resum_slot = (unsigned)b->resum_slot;
   c.resum_per_item = b->resum_per_item;
   BCK(cudaMemsetAsync(b->claimed, 0, sizeof(unsigned) * b->n_jobs, b->stream));
-  BCK(cudaMemsetAsync(b->done, 0, sizeof(unsigned) * (b->n * PH_COUNT + 1), b->stream));
+  BCK(cudaMemsetAsync(b->done, 0, sizeof(unsigned) * (b->n * PH_COUNT * kSets + 1), b->stream));
   BCK(cudaMemsetAsync(b->cur, 0, sizeof(int), b->stream));
   BCK(cudaMemsetAsync(b->error, 0, sizeof(unsigned), b->stream));
   const Inst<T>* insts = (const Inst<T>*)b->insts;
