@@ -396,7 +396,8 @@ __device__ __forceinline__ void med32(const MarchArgs<float>& p, int l, float u,
 template <bool MULTI, bool CUBIC>
 __device__ __forceinline__ Ray2 rhs2(const MarchArgs<float>& p, int l, f2 u2, f2 kap, f2 m2kap,
                                      f2 mkap, f2 pb, f2 mpb, float pb2, f2 pb2v, f2 ihh,
-                                     f2 mihh, f2 ihq, const Ray2& y, unsigned& st) {
+                                     f2 mihh, f2 ihq, const Ray2& y, unsigned& st, float& mnP,
+                                     float& mnZ) {
   float ua, ub;
   sp2(u2, ua, ub);
   float ea, d1a, d2a, eb, d1b, d2b;
@@ -408,11 +409,14 @@ __device__ __forceinline__ Ray2 rhs2(const MarchArgs<float>& p, int l, f2 u2, f2
   const f2 D = fma2(y.dQ, sub2(m2kap, y.dQ), e);           // e - dQ (2 kappa + dQ)
   float P2a, P2b;
   sp2(add2(pb2v, D), P2a, P2b);
-  if (!(P2a > 0.f)) { st |= ST_TURNING; P2a = pb2; }
-  if (!(P2b > 0.f)) { st |= ST_TURNING; P2b = pb2; }
+  // Turning points (P^2 <= 0) and caustics (Z_s <= 0) at any stage: running
+  // minima, checked once after the march (a ray that meets one goes on with
+  // NaN values; its table positions are clamped, its status is an error).
   float Zsa, Zsb;
   sp2(y.Zs, Zsa, Zsb);
-  if (!(Zsa > 0.f) || !(Zsb > 0.f)) st |= ST_CAUSTIC;
+  mnP = fminf(mnP, fminf(P2a, P2b));
+  mnZ = fminf(mnZ, fminf(Zsa, Zsb));
+  (void)pb2;
   const float iPa = rsqrtf(P2a), iPb = rsqrtf(P2b);
   const f2 iP = mk2(iPa, iPb);
   const f2 P = mul2(mk2(P2a, P2b), iP);
@@ -503,21 +507,22 @@ __device__ __forceinline__ void march_x2_body(const MarchArgs<float>& p, int blk
   // RK4: y + h/6 k1 + h/3 k2 + h/3 k3 + h/6 k4, accumulated as the stages
   // complete (k1..k3 need not stay live)
   const f2 h3 = bc2(p.h / 3.f);
+  float mnP = 1.f, mnZ = 1.f;   // smallest P^2 and Z_s met (1: none below)
   for (int n = 0; n < p.Nt; ++n) {
     const Ray2 k1 = rhs2<MULTI, CUBIC>(p, 2 * n, pos(y), kv, m2kap, mkap, pbv, mpb, pb2, pb2v, ihh,
-                                mihh, ihq, y, st);
+                                mihh, ihq, y, st, mnP, mnZ);
     Ray2 acc = axpy2(y, h6, k1);
     const Ray2 y2 = axpy2(y, hh, k1);
     const Ray2 k2 = rhs2<MULTI, CUBIC>(p, 2 * n + 1, pos(y2), kv, m2kap, mkap, pbv, mpb, pb2, pb2v,
-                                ihh, mihh, ihq, y2, st);
+                                ihh, mihh, ihq, y2, st, mnP, mnZ);
     acc = axpy2(acc, h3, k2);
     const Ray2 y3 = axpy2(y, hh, k2);
     const Ray2 k3 = rhs2<MULTI, CUBIC>(p, 2 * n + 1, pos(y3), kv, m2kap, mkap, pbv, mpb, pb2, pb2v,
-                                ihh, mihh, ihq, y3, st);
+                                ihh, mihh, ihq, y3, st, mnP, mnZ);
     acc = axpy2(acc, h3, k3);
     const Ray2 y4 = axpy2(y, h, k3);
     const Ray2 k4 = rhs2<MULTI, CUBIC>(p, 2 * n + 2, pos(y4), kv, m2kap, mkap, pbv, mpb, pb2, pb2v,
-                                ihh, mihh, ihq, y4, st);
+                                ihh, mihh, ihq, y4, st, mnP, mnZ);
     y = axpy2(acc, h6, k4);
     if (PLANES && (n + 1) % p.plane_steps == 0 && n + 1 < p.Nt) {
       const long long po = (long long)((n + 1) / p.plane_steps - 1) * p.NRT * p.Mr;
@@ -525,11 +530,14 @@ __device__ __forceinline__ void march_x2_body(const MarchArgs<float>& p, int blk
     }
   }
   land(2 * p.Nt, p.out_d, p.out_ph, p.out_a);
+  if (!(mnP > 0.f)) st |= ST_TURNING;
+  if (!(mnZ > 0.f)) st |= ST_CAUSTIC;
   if (st) atomicOr(p.status, st);
 }
 
+// 4 CTAs of 256 threads per SM (64 registers)
 template <bool MULTI, bool PLANES, bool CUBIC>
-__global__ void __launch_bounds__(256) k_march_x2(const MarchArgs<float> p) {
+__global__ void __launch_bounds__(256, 4) k_march_x2(const MarchArgs<float> p) {
   march_x2_body<MULTI, PLANES, CUBIC>(p, blockIdx.x, threadIdx.x);
 }
 

@@ -223,11 +223,13 @@ swkb_status upload(swkb_plan* p, void** dst, const std::vector<double>& v) {
 swkb_status swkb::status_from_bits(unsigned bits) {
   if (bits & ST_BOUNDS)
     return fail(SWKB_ERR_CUDA, "a device index left its buffer (bounds-checked build)");
+  // a turning point comes first: the FP32 march carries a ray that met one
+  // on with NaN values, whose landings then also fail the order check
+  if (bits & ST_TURNING) return fail(SWKB_ERR_TURNING, "turning point on a ray (eps - Q^2 <= 0)");
   if (bits & ST_CAUSTIC)
     return fail(SWKB_ERR_CAUSTIC,
                 "caustic between screens (Z_s <= 0 or ray landings out of order); "
                 "use a smaller screen spacing");
-  if (bits & ST_TURNING) return fail(SWKB_ERR_TURNING, "turning point on a ray (eps - Q^2 <= 0)");
   if (bits & ST_RANGE) return fail(SWKB_ERR_RANGE, "a ray left the permittivity table");
   if (bits & ST_COVER) return fail(SWKB_ERR_RANGE, "ghost rays do not cover the screen");
   return SWKB_OK;
