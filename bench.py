@@ -61,6 +61,12 @@ def parse_args():
                     help="fixed launch shapes of the mixed plan (tile_points, ctas_per_sm, "
                          "fft_n1, as the JSON line's \"tiling\" reports them) instead of "
                          "autotuning: a profiler run then times the shapes a plain run chose")
+    ap.add_argument("--case", choices=("plan4", "batch8"), default=None,
+                    help="instead of the benchmark, run one small profiling case twice and exit "
+                         "(no JSON line): plan4 = 4 screens of the bench workload's mixed plan "
+                         "(shapes from --tiling, else autotuned); batch8 = the first 8 "
+                         "instances of the uneven batch, 12 screens each, in one persistent "
+                         "launch")
     ap.add_argument("--large", action="store_true",
                     help="instead of the benchmark, time the paper-scale range-dependent duct "
                          "and the full uneven batch once (one JSON line; minutes)")
@@ -302,14 +308,24 @@ def device_peaks(dev_index, sm_max_mhz):
             "mufu_src": src.format(f"{MUFU_PER_SM_CLK} MUFU ops/clk (nominal)")}
 
 
+KERNEL_SOURCES = ("swkb_device.cuh", "swkb_kernels.cu", "swkb_internal.h")
+
+
+def kernel_source_digest():
+    """16 hex digits of the SHA-256 of the device-code sources, in order."""
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2301_03814_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def kernel_traffic(kind):
     """DRAM bytes per launch from the committed ncu summary, when it was taken
     on the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
-    src = os.path.join(ROOT, "paper_2301_03814_gb300", "csrc", "swkb_kernels.cu")
     try:
         rec = json.load(open(path))
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        digest = kernel_source_digest()
         if rec.get("kernels_sha256_16") != digest:
             return None
         return rec.get("bytes_per_launch", {}).get(kind)
@@ -455,10 +471,10 @@ def batched_measurement(swkb, dev, n=64, seed=4, server_screens=10):
     (swkb_batch_run, autotuned per-instance tiles, plans and queue built
     before the timed region; one warm-up run captures the launch's graph),
     CUDA events on the batch's stream; end to end with host buffers beside
-    it.  The same instances' first 10 screens are also run both ways --
-    through the persistent launch and through the request server (continuous
-    batching, one plan and stream per request, plan creation included) -- for
-    comparison."""
+    it.  For comparison the same instances also run through the request
+    server (continuous batching, one plan and two streams per request, plan
+    creation included), at full ranges and for their first 10 screens, and
+    the first 10 screens through the persistent launch."""
     import torch
     from paper_2301_03814_gb300 import workloads as w
     full = w.batch_uneven(seed, n)
@@ -509,14 +525,16 @@ def batched_measurement(swkb, dev, n=64, seed=4, server_screens=10):
     rec[f"first_{server_screens}_screens_persistent_screen_points_per_s"] = \
         pts_s / (e0.elapsed_time(e1) / 1e3)
     bs.close()
-    srv = swkb.Server(96 << 30, max_slots=16)
-    t0 = time.perf_counter()
-    tickets = [srv.submit(pb, swkb.SWKB_MIXED)[1] for pb in short]
-    sts = [srv.poll(t, timeout_ms=-1)[0] for t in tickets]
-    dt = time.perf_counter() - t0
-    srv.close()
-    rec[f"first_{server_screens}_screens_server_screen_points_per_s"] = pts_s / dt
-    rec["server_ok"] = int(sum(x == 0 for x in sts))
+    for label, jobs, pts_j in (("first_%d_screens" % server_screens, short, pts_s),
+                               ("full_ranges", full, pts)):
+        srv = swkb.Server(96 << 30, max_slots=16)
+        t0 = time.perf_counter()
+        tickets = [srv.submit(pb, swkb.SWKB_MIXED)[1] for pb in jobs]
+        sts = [srv.poll(t, timeout_ms=-1)[0] for t in tickets]
+        dt = time.perf_counter() - t0
+        srv.close()
+        rec[f"{label}_server_screen_points_per_s"] = pts_j / dt
+        rec[f"{label}_server_ok"] = int(sum(x == 0 for x in sts))
     return rec
 
 
@@ -900,8 +918,33 @@ def run_large():
     return 0
 
 
+def run_case(args):
+    """A small case for profilers (ncu -k <kernel> -s <skip> -c <count>)."""
+    import torch
+    from paper_2301_03814_gb300 import swkb
+    from paper_2301_03814_gb300 import workloads as w
+    if args.case == "plan4":
+        pb = workload().with_(n_screens=4)
+        fixed = tuple(int(v) for v in args.tiling.split(",")) if args.tiling else None
+        plan = swkb.Plan(pb, swkb.SWKB_MIXED, autotune=fixed is None, tiling=fixed)
+        u = torch.from_numpy(pb.u0).cuda()
+        out = torch.empty_like(u)
+        for _ in range(2):
+            plan.propagate_device(u.data_ptr(), out.data_ptr())
+    else:
+        pbs = [pb.with_(n_screens=min(pb.n_screens, 12)) for pb in w.batch_uneven(4, 64)[:8]]
+        b = swkb.Batch(pbs, swkb.SWKB_MIXED)
+        out = torch.empty(b.total, dtype=torch.complex128, device="cuda")
+        for _ in range(2):
+            b.run_device(None, out.data_ptr())
+    torch.cuda.synchronize()
+    return 0
+
+
 def main():
     args = parse_args()
+    if args.case:
+        return run_case(args)
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         return run_reference(args, rank, world)
