@@ -33,6 +33,7 @@ import numpy as np
 BC_PERIODIC = 0
 BC_NEUMANN = 1
 BC_DIRICHLET = 2
+BC_OPEN = 3        # non-periodic, field vanishing near both ends (patch-wise continuation)
 
 
 @dataclass
@@ -63,7 +64,10 @@ class Problem:
 
     z_a, z_b   physical vertical extent; n_z points z_a + m*(z_b-z_a)/n_z.
     bc         BC_PERIODIC: period [z_a, z_b); BC_NEUMANN/BC_DIRICHLET: ground
-               at z_a, solved on the mirrored period [2 z_a - z_b, z_b).
+               at z_a, solved on the mirrored period [2 z_a - z_b, z_b);
+               BC_OPEN: [z_a, z_b) is not periodic and the field vanishes near
+               both ends; it is expanded patch by patch (fc_patch points per
+               patch, fc_overlap shared by neighbours).
     x0, dx     first screen position and screen spacing.
     theta_max  largest kept plane-wave angle (radians); n_max overrides if > 0.
     """
@@ -83,6 +87,8 @@ class Problem:
     rk4_steps: int
     absorber_frac: float = 0.0
     n_max: int = 0
+    fc_patch: int = 0      # BC_OPEN: grid points per continuation patch
+    fc_overlap: int = 0    # BC_OPEN: grid points shared by neighbouring patches
     meta: dict = field(default_factory=dict)
 
     def with_(self, **kw) -> "Problem":
