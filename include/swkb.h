@@ -64,7 +64,11 @@ typedef enum {
   SWKB_ERR_CANCELLED = 10    /* request cancelled                            */
 } swkb_status;
 
-enum { SWKB_BC_PERIODIC = 0, SWKB_BC_NEUMANN = 1, SWKB_BC_DIRICHLET = 2 };
+/* SWKB_BC_OPEN: the overlapping Fourier-continuation method of Sec. 2.2 (Eq.
+ * ifft_eq_phi_patches): [z_a, z_b) is not periodic, the field must vanish
+ * near both ends, and each screen expands it patch by patch (fc_patch grid
+ * points per patch, fc_overlap shared by neighbours; see swkb_options). */
+enum { SWKB_BC_PERIODIC = 0, SWKB_BC_NEUMANN = 1, SWKB_BC_DIRICHLET = 2, SWKB_BC_OPEN = 3 };
 enum { SWKB_FP64 = 0, SWKB_MIXED = 1 };
 
 /*
@@ -138,6 +142,20 @@ typedef struct {
   int32_t tile_points;    /* grid points per resummation tile                 */
   int32_t ctas_per_sm;    /* resummation CTAs per SM the mode groups target   */
   int32_t fft_n1;         /* DFT split N = fft_n1 * (N / fft_n1)              */
+  /* SWKB_BC_OPEN only (ignored otherwise).  Patch p holds the grid points
+     p (fc_patch - fc_overlap) .. p (fc_patch - fc_overlap) + fc_patch - 1;
+     the patches must tile the n_z points exactly, 2 <= fc_overlap,
+     2 fc_overlap <= fc_patch and fc_patch + 25 <= 2048.  Each patch's
+     samples are continued by FC-Gram (5 matching points, 25 continuation
+     points) to a sequence of N_p = fc_patch + 25 points whose DFT gives the
+     patch's modes (kappa_n = 2 pi n / (k N_p dz), |n| <= floor(sin(theta_max)
+     N_p dz / lambda) or n_max); the partition of unity S^p rises and falls
+     over fc_overlap points (a C-infinity step), also at the interval's two
+     ends; every ray of mode n launched at z_j carries
+     sum_p S^p(z_j) w_n^p / N_p.  No absorber, no inner planes, no autotune;
+     swkb_debug_screen and the batch kernel refuse these plans. */
+  int32_t fc_patch;
+  int32_t fc_overlap;
 } swkb_options;
 
 typedef struct {
@@ -160,6 +178,10 @@ typedef struct {
                              interval the march evaluates (0: the quintic
                              itself; always 0 for FP64 plans)                 */
   int32_t ctas_per_sm;    /* resummation CTAs per SM the mode groups target  */
+  int32_t fc_patches;     /* SWKB_BC_OPEN: patches (else 0); n_fft is then n_z
+                             rounded up to 256 (the points the rays cover and
+                             the sum runs over) and period the patches' N_p dz */
+  int32_t fc_period_points; /* SWKB_BC_OPEN: N_p = fc_patch + 25 (else 0)     */
 } swkb_plan_info;
 
 /* Fill *opt with defaults: FP64, theta_max 30 deg, R 1, N_t 8, no absorber. */
@@ -170,7 +192,8 @@ void swkb_options_default(swkb_options* opt);
  * layout, uploads the permittivity table and allocates every device buffer
  * (all allocation happens here).  n_z physical points; screen_dx the screen
  * spacing.  The FFT length (n_z, or 2 n_z when grounded) must be a power of
- * two between 64 and 2^20.  Returns SWKB_ERR_INVALID_ARG on bad shapes, on a
+ * two between 64 and 2^20 (SWKB_BC_OPEN: any n_z in [64, 2^20 - 256] that the
+ * patches tile).  Returns SWKB_ERR_INVALID_ARG on bad shapes, on a
  * table that does not cover the rays' reach, or on a mode evanescent at the
  * reference permittivity.
  */

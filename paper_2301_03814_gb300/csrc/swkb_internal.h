@@ -139,6 +139,42 @@ struct FftArgs {
   typename C2<T>::type* cpol;        // [M] (|c_n|, arg(c_n) / 2 pi), or nullptr
 };
 
+// Patch-wise Fourier-continuation screens (swkb_fc.cu).  Patch p holds the
+// grid points p stride .. p stride + n_pat - 1 of the non-periodic interval.
+template <typename T>
+struct FcModesArgs {
+  const typename C2<T>::type* u;     // [>= n_z] the screen field
+  int n_pat, stride, P, Np, n_max, M;
+  const double* cont;                // [FC_C][FC_D] continuation operator
+  const double2* tw;                 // [Np] exp(-2 pi i k / Np)
+  const typename C2<T>::type* ephi;  // [M] exp(i k dx Pbar_n)
+  double inv_Np;
+  typename C2<T>::type* cf;          // [P][M] out: rotated, carried mode coefficients
+};
+
+template <typename T>
+struct FcResumArgs {
+  const T* d;                        // [NRT][M] rays, as for the periodic resummation
+  const T* ph;
+  const T* a;
+  const int* jlo;                    // [n_tiles + 1][M]
+  const typename C2<T>::type* cf;    // [P][M]
+  const int* win_p;                  // [NRT] first patch with a non-zero weight at ray j
+  const typename C2<T>::type* win_s; // [NRT] (S^{p0}, S^{p0+1}) at ray j
+  int M, NRT, G, R, N, TM, n_tiles, n_groups, modes_per_group, n_max, wcap, Np, P;
+  typename C2<T>::type* part;        // [n_groups][N]
+  unsigned* status;
+};
+
+template <typename T> cudaError_t launch_fc_modes(const FcModesArgs<T>& a, cudaStream_t s);
+template <typename T> cudaError_t launch_fc_resum(const FcResumArgs<T>& a, cudaStream_t s);
+template <typename T> size_t fc_resum_smem_bytes(int wcap, int tile_points);
+template <typename T> size_t fc_modes_smem_bytes(int Np);
+template <typename T> cudaError_t prepare_fc_kernels(int resum_smem, int modes_smem);
+// The FC-Gram continuation operator ([FC_C][FC_D], row-major) and its sizes.
+const double* fc_continuation_host();
+constexpr int FC_CONT_ROWS = 25, FC_CONT_COLS = 5;
+
 // launchers (defined in swkb_kernels.cu for T = float, double)
 template <typename T> cudaError_t launch_init(const double* u0, int n_z, int N, int mirror,
                                               typename C2<T>::type* u, cudaStream_t s);

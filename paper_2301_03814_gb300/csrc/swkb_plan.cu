@@ -166,6 +166,15 @@ struct swkb_plan {
   void* ra1 = nullptr;
   int* jlo1 = nullptr;
   int* jlo_neg1 = nullptr;
+  // patch-wise Fourier continuation (SWKB_BC_OPEN): patches of fc_pat grid
+  // points every fc_stride points, fc_P of them, each continued to fc_Np
+  bool fc = false;
+  int fc_pat = 0, fc_ov = 0, fc_stride = 0, fc_P = 0, fc_Np = 0;
+  void* fc_cont = nullptr;    // [FC_C][FC_D] continuation operator, FP64
+  void* fc_tw = nullptr;      // [Np] exp(-2 pi i k / Np), FP64
+  void* fc_cf = nullptr;      // [P][M] mode coefficients of every patch
+  int* fc_win_p = nullptr;    // [NRT] first patch weighting launch point j
+  void* fc_win_s = nullptr;   // [NRT] (S^{p0}, S^{p0+1}) at launch point j
 };
 
 namespace {
@@ -384,6 +393,65 @@ int pieces_for(const swkb_plan* p, const swkb_profile* prof) {
   return S;
 }
 
+// C-infinity step of the partition of unity: e^{-1/t} / (e^{-1/t} + e^{-1/(1-t)}),
+// 0 for t <= 0, 1 for t >= 1.
+double fc_step(double t) {
+  if (t <= 0.0) return 0.0;
+  if (t >= 1.0) return 1.0;
+  const double a = exp(-1.0 / t), b = exp(-1.0 / (1.0 - t));
+  return a / (a + b);
+}
+
+// Weight of patch pt at grid-unit position u: rising over the patch's first
+// fc_ov points, falling over its last fc_ov, zero outside it.
+double fc_weight(const swkb_plan* p, int pt, double u) {
+  const double s = (double)pt * p->fc_stride, e = s + p->fc_pat - 1, w = p->fc_ov - 1;
+  return fc_step((u - s) / w) * (1.0 - fc_step((u - (e - w)) / w));
+}
+
+// Continuation operator, patch twiddles, per-launch-point patch weights and
+// the per-patch coefficient buffer of a patch-wise plan.
+template <typename T>
+swkb_status build_fc(swkb_plan* p) {
+  using V = typename C2<T>::type;
+  {
+    const double* op = fc_continuation_host();
+    std::vector<double> cont(op, op + FC_CONT_ROWS * FC_CONT_COLS);
+    TRY(upload<double>(p, &p->fc_cont, cont));
+  }
+  {
+    std::vector<double> tw(2 * (size_t)p->fc_Np);
+    for (int k = 0; k < p->fc_Np; ++k) {
+      const double a = 2.0 * M_PI * ((double)k / p->fc_Np);
+      tw[2 * k] = cos(a);
+      tw[2 * k + 1] = -sin(a);
+    }
+    TRY(upload<double>(p, &p->fc_tw, tw));
+  }
+  {
+    // launch point j sits at grid position (j - G) R; at most two patches
+    // weight it: the first with a non-zero weight and the next one
+    std::vector<int> wp(p->NRT, 0);
+    std::vector<double> ws(2 * (size_t)p->NRT, 0.0);
+    for (int j = 0; j < p->NRT; ++j) {
+      const double u = (double)(j - p->G) * p->R;
+      int first = -1;
+      for (int pt = std::max(0, (int)floor((u - p->fc_pat + 1) / p->fc_stride));
+           pt < p->fc_P && pt * (double)p->fc_stride <= u; ++pt)
+        if (fc_weight(p, pt, u) > 0.0) { first = pt; break; }
+      if (first < 0) continue;
+      wp[j] = first;
+      ws[2 * (size_t)j] = fc_weight(p, first, u);
+      ws[2 * (size_t)j + 1] = first + 1 < p->fc_P ? fc_weight(p, first + 1, u) : 0.0;
+    }
+    TRY(dev_alloc(p, (void**)&p->fc_win_p, wp.size() * sizeof(int)));
+    CK(cudaMemcpy(p->fc_win_p, wp.data(), wp.size() * sizeof(int), cudaMemcpyHostToDevice));
+    TRY(upload<T>(p, &p->fc_win_s, ws));
+  }
+  TRY(dev_alloc(p, &p->fc_cf, (size_t)p->fc_P * p->M * sizeof(V)));
+  return SWKB_OK;
+}
+
 template <typename T>
 swkb_status build_device(swkb_plan* p, const swkb_profile* prof) {
   using V = typename C2<T>::type;
@@ -475,8 +543,9 @@ swkb_status build_device(swkb_plan* p, const swkb_profile* prof) {
     TRY(upload<T>(p, &p->pbar2_d, pb2));
     TRY(upload<T>(p, &p->ephi_d, p->ephi));
   }
+  if (p->fc) TRY(build_fc<T>(p));
   // twiddles exp(-2 pi i k / N)
-  {
+  if (!p->fc) {
     std::vector<double> tw(2 * (size_t)N);
     for (int k = 0; k < N; ++k) {
       const double a = 2.0 * M_PI * ((double)k / N);
@@ -502,7 +571,7 @@ swkb_status build_device(swkb_plan* p, const swkb_profile* prof) {
   // work buffers
   TRY(dev_alloc(p, &p->u, (size_t)N * sizeof(V)));
   TRY(dev_alloc(p, &p->part, (size_t)p->alloc_groups * N * sizeof(V)));
-  TRY(dev_alloc(p, &p->Y, (size_t)N * sizeof(V)));
+  if (!p->fc) TRY(dev_alloc(p, &p->Y, (size_t)N * sizeof(V)));
   TRY(dev_alloc(p, &p->c, (size_t)M * sizeof(V)));
   if (sizeof(T) == 4) TRY(dev_alloc(p, &p->cpol, (size_t)M * sizeof(V)));
   const size_t rays = (size_t)p->NRT * p->Mr;
@@ -539,7 +608,11 @@ swkb_status build_device(swkb_plan* p, const swkb_profile* prof) {
   TRY(dev_alloc(p, (void**)&p->status, sizeof(unsigned)));
   CK(cudaMemsetAsync(p->status, 0, sizeof(unsigned), p->stream));
   TRY(dev_alloc(p, (void**)&p->io, 2 * (size_t)std::max(N, p->n_z) * sizeof(double)));
-  CK(prepare_kernels<T>((int)resum_smem_bytes<T>(p->wcap, p->TM)));
+  if (p->fc)
+    CK(prepare_fc_kernels<T>((int)fc_resum_smem_bytes<T>(p->wcap, p->TM),
+                             (int)fc_modes_smem_bytes<T>(p->fc_Np)));
+  else
+    CK(prepare_kernels<T>((int)resum_smem_bytes<T>(p->wcap, p->TM)));
   return SWKB_OK;
 }
 
@@ -698,8 +771,67 @@ FftArgs<T> fft_args(const swkb_plan* p, bool fuse) {
 }
 
 template <typename T>
+FcModesArgs<T> fc_modes_args(const swkb_plan* p) {
+  using V = typename C2<T>::type;
+  FcModesArgs<T> f;
+  f.u = (const V*)p->u;
+  f.n_pat = p->fc_pat; f.stride = p->fc_stride; f.P = p->fc_P; f.Np = p->fc_Np;
+  f.n_max = p->n_max; f.M = p->M;
+  f.cont = (const double*)p->fc_cont;
+  f.tw = (const double2*)p->fc_tw;
+  f.ephi = (const V*)p->ephi_d;
+  f.inv_Np = 1.0 / p->fc_Np;
+  f.cf = (V*)p->fc_cf;
+  return f;
+}
+
+template <typename T>
+FcResumArgs<T> fc_resum_args(const swkb_plan* p, const T* d, const T* ph, const T* a,
+                             const int* jlo) {
+  using V = typename C2<T>::type;
+  FcResumArgs<T> r;
+  r.d = d; r.ph = ph; r.a = a; r.jlo = jlo;
+  r.cf = (const V*)p->fc_cf;
+  r.win_p = p->fc_win_p;
+  r.win_s = (const V*)p->fc_win_s;
+  r.M = p->M; r.NRT = p->NRT; r.G = p->G; r.R = p->R; r.N = p->N; r.TM = p->TM;
+  r.n_tiles = p->n_tiles; r.n_groups = p->n_groups; r.modes_per_group = p->modes_per_group;
+  r.n_max = p->n_max; r.wcap = p->wcap; r.Np = p->fc_Np; r.P = p->fc_P;
+  r.part = (V*)p->part; r.status = p->status;
+  return r;
+}
+
+// One patch-wise screen (Sec. 2.2): partials -> field, the patches' FC
+// modes, rays, brackets, and the sum with per-ray complex amplitudes.
+template <typename T>
+swkb_status fc_screen(swkb_plan* p, int q, bool u_fresh) {
+  using V = typename C2<T>::type;
+  cudaStream_t s = p->stream;
+  if (!u_fresh) {
+    ReduceArgs<T> r{(const V*)p->part, p->n_groups, p->N, nullptr, 0, 0, (V*)p->u};
+    TRY(timed(p, SWKB_KERNEL_REDUCE, 1, [&] { return launch_reduce<T>(r, s); }));
+  }
+  const FcModesArgs<T> f = fc_modes_args<T>(p);
+  TRY(timed(p, SWKB_KERNEL_FFT, 1, [&] { return launch_fc_modes<T>(f, s); }));
+  const MarchArgs<T> ma = march_args<T>(p, q);
+  const bool multi = p->n_cols > 1;
+  const bool march = !(p->reuse_rays && p->rays_ready);
+  if (march)
+    TRY(timed(p, SWKB_KERNEL_MARCH, 1, [&] { return launch_march<T>(ma, multi, s); }));
+  const BracketArgs<T> b = bracket_args<T>(p, (const T*)p->rd);
+  if (march) TRY(timed(p, SWKB_KERNEL_BRACKET, 1, [&] { return launch_bracket<T>(b, s); }));
+  p->rays_ready = true;
+  const FcResumArgs<T> ra = fc_resum_args<T>(p, (const T*)p->rd, (const T*)p->rph,
+                                             (const T*)p->ra, p->jlo);
+  TRY(timed(p, SWKB_KERNEL_RESUM, 1, [&] { return launch_fc_resum<T>(ra, s); }));
+  p->stats.screens += 1;
+  return SWKB_OK;
+}
+
+template <typename T>
 swkb_status launch_screen(swkb_plan* p, int q, bool u_fresh) {
   Range range("swkb_screen");
+  if (p->fc) return fc_screen<T>(p, q, u_fresh);
   using V = typename C2<T>::type;
   cudaStream_t s = p->stream;
   // with a two-pass DFT, pass 1 forms the field from the partials itself
@@ -772,7 +904,8 @@ swkb_status enqueue(swkb_plan* p, const double* u0, int q0, int n, double* out_d
   const int off = p->mirror ? p->n_z : 0;
   const size_t nb = 2 * sizeof(double) * p->n_z;
   TRY(timed(p, SWKB_KERNEL_INIT, 1,
-            [&] { return launch_init<T>(u0, p->n_z, p->N, p->mirror, (V*)p->u, p->stream); }));
+            [&] { return launch_init<T>(u0, p->n_z, p->fc ? p->n_z : p->N, p->mirror, (V*)p->u,
+                                        p->stream); }));
   bool fresh = true;
   int k = 0;
   auto emit = [&](int idx) -> swkb_status {
@@ -820,6 +953,22 @@ swkb_status overlapped_screen(swkb_plan* p, int q, int b, bool fresh) {
   ma.out_d = rd[b]; ma.out_ph = rph[b]; ma.out_a = ra[b];
   TRY(timed_on(p, sr, SWKB_KERNEL_MARCH, 1, [&] { return launch_march<T>(ma, multi, sr); }));
   CK(cudaEventRecord(p->ev_rays[b], sr));
+  if (p->fc) {
+    if (!fresh) {
+      ReduceArgs<T> r{(const V*)p->part, p->n_groups, p->N, nullptr, 0, 0, (V*)p->u};
+      TRY(timed(p, SWKB_KERNEL_REDUCE, 1, [&] { return launch_reduce<T>(r, s); }));
+    }
+    const FcModesArgs<T> fm = fc_modes_args<T>(p);
+    TRY(timed(p, SWKB_KERNEL_FFT, 1, [&] { return launch_fc_modes<T>(fm, s); }));
+    CK(cudaStreamWaitEvent(s, p->ev_rays[b], 0));
+    const BracketArgs<T> br = bracket_args<T>(p, rd[b], jlo[b], jneg[b]);
+    TRY(timed(p, SWKB_KERNEL_BRACKET, 1, [&] { return launch_bracket<T>(br, s); }));
+    const FcResumArgs<T> rs = fc_resum_args<T>(p, rd[b], rph[b], ra[b], jlo[b]);
+    TRY(timed(p, SWKB_KERNEL_RESUM, 1, [&] { return launch_fc_resum<T>(rs, s); }));
+    CK(cudaEventRecord(p->ev_free[b], s));
+    p->stats.screens += 1;
+    return SWKB_OK;
+  }
   // modes of screen q (pass 1 forms the field from the partials itself)
   const bool fuse = p->fuse_reduce && !fresh && p->N1 > 1 && (p->sym || !p->mirror);
   if (!fresh && !fuse) {
@@ -867,7 +1016,8 @@ swkb_status enqueue_overlapped(swkb_plan* p, const double* u0, int q0, int n, do
   const int off = p->mirror ? p->n_z : 0;
   const size_t nb = 2 * sizeof(double) * p->n_z;
   TRY(timed(p, SWKB_KERNEL_INIT, 1,
-            [&] { return launch_init<T>(u0, p->n_z, p->N, p->mirror, (V*)p->u, s); }));
+            [&] { return launch_init<T>(u0, p->n_z, p->fc ? p->n_z : p->N, p->mirror, (V*)p->u,
+                                        s); }));
   // both sets start free (this also forks ray_stream from the plan stream)
   CK(cudaEventRecord(p->ev_free[0], s));
   CK(cudaEventRecord(p->ev_free[1], s));
@@ -1210,6 +1360,7 @@ struct Tiling {
 
 bool valid_tiling(const swkb_plan* p, const Tiling& t) {
   if (t.PW != 2 && t.PW != 4 && t.PW != 8 && t.PW != 16) return false;
+  if (p->fc && (t.PW > 8 || p->N % (32 * t.PW))) return false;
   if (32 * t.PW > (p->sym ? p->N / 2 : p->N)) return false;
   if (t.N1 < 1 || t.N1 > 64 || (t.N1 & (t.N1 - 1)) || t.N1 > p->N / 32) return false;
   return t.ctas_per_sm >= 1;
@@ -1261,7 +1412,7 @@ swkb_status configure(swkb_plan* p, const swkb_profile* prof, double k, const sw
   if (!(k > 0) || !std::isfinite(k)) return fail(SWKB_ERR_INVALID_ARG, "k must be > 0");
   if (!(dom->z_b > dom->z_a)) return fail(SWKB_ERR_INVALID_ARG, "need z_b > z_a");
   if (!(screen_dx > 0)) return fail(SWKB_ERR_INVALID_ARG, "screen spacing must be > 0");
-  if (dom->bc < SWKB_BC_PERIODIC || dom->bc > SWKB_BC_DIRICHLET)
+  if (dom->bc < SWKB_BC_PERIODIC || dom->bc > SWKB_BC_OPEN)
     return fail(SWKB_ERR_INVALID_ARG, "unknown boundary condition %d", dom->bc);
   if (opt.precision != SWKB_FP64 && opt.precision != SWKB_MIXED)
     return fail(SWKB_ERR_INVALID_ARG, "unknown precision %d", opt.precision);
@@ -1282,16 +1433,43 @@ swkb_status configure(swkb_plan* p, const swkb_profile* prof, double k, const sw
   p->k = k; p->z_a = dom->z_a; p->z_b = dom->z_b; p->x0 = dom->x0; p->dx = screen_dx;
   p->n_z = n_z;
   const double H = dom->z_b - dom->z_a;
-  p->N = p->mirror ? 2 * n_z : n_z;
-  if (n_z < 1 || !is_pow2(p->N) || p->N < 64 || p->N > (1 << 20))
-    return fail(SWKB_ERR_INVALID_ARG, "FFT length %d must be a power of two in [64, 2^20]", p->N);
-  p->L = p->mirror ? 2 * H : H;
+  p->fc = dom->bc == SWKB_BC_OPEN;
+  if (p->fc) {
+    // patch-wise continuation: the rays and the sum cover n_z rounded up to
+    // whole resummation tiles; the extra points belong to no patch
+    p->fc_pat = opt.fc_patch;
+    p->fc_ov = opt.fc_overlap;
+    p->fc_stride = p->fc_pat - p->fc_ov;
+    if (n_z < 64 || n_z > (1 << 20) - 256)
+      return fail(SWKB_ERR_INVALID_ARG, "n_z %d must be in [64, 2^20 - 256]", n_z);
+    if (p->fc_ov < 2 || p->fc_pat < 2 * p->fc_ov || p->fc_pat > n_z ||
+        (n_z - p->fc_pat) % p->fc_stride)
+      return fail(SWKB_ERR_INVALID_ARG,
+                  "patches (fc_patch %d, fc_overlap %d) must satisfy 2 <= fc_overlap, "
+                  "2 fc_overlap <= fc_patch <= n_z and tile n_z = %d exactly",
+                  p->fc_pat, p->fc_ov, n_z);
+    p->fc_Np = p->fc_pat + FC_CONT_ROWS;
+    if (p->fc_Np > 2048)
+      return fail(SWKB_ERR_INVALID_ARG, "fc_patch + %d = %d exceeds 2048", FC_CONT_ROWS,
+                  p->fc_Np);
+    p->fc_P = (n_z - p->fc_pat) / p->fc_stride + 1;
+    if (opt.absorber_frac != 0.0 || opt.planes > 1)
+      return fail(SWKB_ERR_INVALID_ARG, "patch-wise plans take no absorber and no inner planes");
+    p->N = (n_z + 255) / 256 * 256;
+    p->L = p->fc_Np * (H / n_z);
+  } else {
+    p->N = p->mirror ? 2 * n_z : n_z;
+    if (n_z < 1 || !is_pow2(p->N) || p->N < 64 || p->N > (1 << 20))
+      return fail(SWKB_ERR_INVALID_ARG, "FFT length %d must be a power of two in [64, 2^20]",
+                  p->N);
+    p->L = p->mirror ? 2 * H : H;
+  }
   p->dz = H / n_z;
   p->z_lo = p->mirror ? dom->z_a - H : dom->z_a;
   const double lam = 2.0 * M_PI / k;
   if (opt.n_max > 0) p->n_max = opt.n_max;
   else p->n_max = (int)floor(sin(opt.theta_max) * p->L / lam * (1.0 + 1e-12));
-  p->n_max = std::min(p->n_max, p->N / 2 - 1);
+  p->n_max = std::min(p->n_max, (p->fc ? p->fc_Np : p->N) / 2 - 1);
   if (p->n_max < 0) return fail(SWKB_ERR_INVALID_ARG, "negative theta_max or n_max");
   p->M = 2 * p->n_max + 1;
   p->R = opt.ray_stride;
@@ -1358,7 +1536,7 @@ swkb_status configure(swkb_plan* p, const swkb_profile* prof, double k, const sw
   p->device = opt.device;
   CK(cudaSetDevice(p->device));
   CK(cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device));
-  p->autotune = opt.autotune != 0;
+  p->autotune = opt.autotune != 0 && !p->fc;
   p->reuse_rays = opt.reuse_rays != 0 && p->n_cols == 1;
   // rays on a second stream unless they are reused (SWKB_OVERLAP=0: one
   // stream, one ray-buffer set)
@@ -1383,8 +1561,12 @@ swkb_status configure(swkb_plan* p, const swkb_profile* prof, double k, const sw
   {
     int optin = 0;
     CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
-    const size_t smem = p->precision == SWKB_FP64 ? resum_smem_bytes<double>(p->wcap, p->TM)
-                                                  : resum_smem_bytes<float>(p->wcap, p->TM);
+    const bool f64 = p->precision == SWKB_FP64;
+    size_t smem = p->fc ? (f64 ? fc_resum_smem_bytes<double>(p->wcap, p->TM)
+                               : fc_resum_smem_bytes<float>(p->wcap, p->TM))
+                        : (f64 ? resum_smem_bytes<double>(p->wcap, p->TM)
+                               : resum_smem_bytes<float>(p->wcap, p->TM));
+    if (p->fc) smem = std::max(smem, fc_modes_smem_bytes<double>(p->fc_Np));
     if (smem > (size_t)optin)
       return fail(SWKB_ERR_INVALID_ARG, "resummation tile of %d points needs %zu B of shared "
                   "memory (%d available)", p->TM, smem, optin);
@@ -1422,6 +1604,12 @@ size_t device_bytes(const swkb_plan* p) {
   b += (size_t)(p->alloc_tiles + 1) * p->Mr * sizeof(int) * (p->sym ? 2 : 1) *
        (p->overlap ? 2 : 1);
   b += 16 + 2 * (size_t)std::max(p->N, p->n_z) * sizeof(double);   // status, io
+  if (p->fc) {
+    b -= (size_t)p->N * V * 2;                                       // no twiddles, no Y
+    b += (size_t)FC_CONT_ROWS * FC_CONT_COLS * 8 + (size_t)p->fc_Np * 16   // operator, twiddles
+         + (size_t)p->NRT * (sizeof(int) + V)                        // launch-point weights
+         + (size_t)p->fc_P * p->M * V;                               // patch coefficients
+  }
   return b;
 }
 
@@ -1436,7 +1624,8 @@ swkb_status begin_t(swkb_plan* p, const double* u0_host) {
   CK(cudaMemcpyAsync(p->io, u0_host, 2 * sizeof(double) * p->n_z, cudaMemcpyHostToDevice,
                      p->stream));
   TRY(timed(p, SWKB_KERNEL_INIT, 1,
-            [&] { return launch_init<T>(p->io, p->n_z, p->N, p->mirror, (V*)p->u, p->stream); }));
+            [&] { return launch_init<T>(p->io, p->n_z, p->fc ? p->n_z : p->N, p->mirror,
+                                        (V*)p->u, p->stream); }));
   if (p->overlap) {   // both ray-buffer sets free
     CK(cudaEventRecord(p->ev_free[0], p->stream));
     CK(cudaEventRecord(p->ev_free[1], p->stream));
@@ -1553,6 +1742,7 @@ swkb_status plan_parts(swkb_plan* p, PlanParts<T>* o) {
     return fail(SWKB_ERR_INVALID_ARG, "plan precision does not match the batch");
   if (p->planes > 1 || p->reuse_rays)
     return fail(SWKB_ERR_INVALID_ARG, "batched plans march every screen and have no inner planes");
+  if (p->fc) return fail(SWKB_ERR_INVALID_ARG, "the batch kernel runs periodic and grounded plans");
   if (p->N1 < 2)
     return fail(SWKB_ERR_INVALID_ARG, "batched plans need a two-pass DFT (fft_n1 >= 2)");
   *o = PlanParts<T>{};
@@ -1724,6 +1914,8 @@ swkb_status swkb_plan_get_info(const swkb_plan* p, swkb_plan_info* info) {
   info->device_bytes = p->bytes;
   info->medium_pieces = p->pieces;
   info->ctas_per_sm = p->ctas_per_sm;
+  info->fc_patches = p->fc_P;
+  info->fc_period_points = p->fc_Np;
   return SWKB_OK;
 }
 
@@ -1764,6 +1956,7 @@ swkb_status swkb_propagate_planes(swkb_plan* p, const double* u0, int32_t q0, in
   try {
     if (!p || !u0 || !u_out) return fail(SWKB_ERR_INVALID_ARG, "NULL argument");
     if (n_screens < 0 || q0 < 0) return fail(SWKB_ERR_INVALID_ARG, "negative screen count");
+    if (p->fc) return fail(SWKB_ERR_INVALID_ARG, "patch-wise plans have no inner planes");
     if (planes < 1 || p->Nt % planes)
       return fail(SWKB_ERR_INVALID_ARG, "planes (%d) must divide rk4_steps (%d)", planes, p->Nt);
     if (planes > std::max(1, p->planes))
@@ -1795,6 +1988,7 @@ swkb_status swkb_debug_screen(swkb_plan* p, int32_t q, const double* u_full, dou
                               double* delta, double* r, double* a, double* u_next) {
   try {
     if (!p || !u_full) return fail(SWKB_ERR_INVALID_ARG, "NULL argument");
+    if (p->fc) return fail(SWKB_ERR_INVALID_ARG, "patch-wise plans have no single mode set");
     CK(cudaSetDevice(p->device));
     return p->precision == SWKB_FP64 ? debug_screen<double>(p, q, u_full, c, delta, r, a, u_next)
                                      : debug_screen<float>(p, q, u_full, c, delta, r, a, u_next);

@@ -29,7 +29,7 @@ SWKB_ERR_AGAIN = 8
 SWKB_NOT_READY = 9
 SWKB_ERR_CANCELLED = 10
 
-SWKB_BC_PERIODIC, SWKB_BC_NEUMANN, SWKB_BC_DIRICHLET = 0, 1, 2
+SWKB_BC_PERIODIC, SWKB_BC_NEUMANN, SWKB_BC_DIRICHLET, SWKB_BC_OPEN = 0, 1, 2, 3
 SWKB_FP64, SWKB_MIXED = 0, 1
 
 KERNEL_KINDS = ("init", "reduce", "fft", "march", "bracket", "resum", "output")
@@ -64,7 +64,8 @@ class swkb_options(ctypes.Structure):
                 ("ray_stride", c_int32), ("rk4_steps", c_int32), ("absorber_frac", c_double),
                 ("autotune", c_int32), ("cuda_stream", c_void_p), ("device", c_int32),
                 ("reuse_rays", c_int32), ("planes", c_int32), ("tile_points", c_int32),
-                ("ctas_per_sm", c_int32), ("fft_n1", c_int32)]
+                ("ctas_per_sm", c_int32), ("fft_n1", c_int32), ("fc_patch", c_int32),
+                ("fc_overlap", c_int32)]
 
 
 class swkb_plan_info(ctypes.Structure):
@@ -73,7 +74,8 @@ class swkb_plan_info(ctypes.Structure):
                 ("tile_points", c_int32), ("mode_groups", c_int32), ("march_modes", c_int32),
                 ("resum_points", c_int32), ("fft_n1", c_int32), ("dz", c_double),
                 ("period", c_double), ("eps_ref", c_double), ("device_bytes", c_size_t),
-                ("medium_pieces", c_int32), ("ctas_per_sm", c_int32)]
+                ("medium_pieces", c_int32), ("ctas_per_sm", c_int32), ("fc_patches", c_int32),
+                ("fc_period_points", c_int32)]
 
 
 class swkb_hill_desc(ctypes.Structure):
@@ -240,6 +242,8 @@ def options_for(problem, precision=SWKB_FP64, stream=None, device=0, autotune=Fa
     o.autotune = 1 if autotune else 0
     o.reuse_rays = 1 if reuse_rays else 0
     o.planes = int(planes)
+    o.fc_patch = int(getattr(problem, "fc_patch", 0))
+    o.fc_overlap = int(getattr(problem, "fc_overlap", 0))
     if tiling is not None:
         o.tile_points, o.ctas_per_sm, o.fft_n1 = (int(v) for v in tiling)
     return o

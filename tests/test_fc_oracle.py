@@ -237,3 +237,21 @@ def test_partition_mutants_are_caught(name, pt, step):
     Pt = right_ramp_rises(F.Patches) if pt == "right" else F.Patches
     with pytest.raises(AssertionError):
         P.pin_partition(Pt, step)
+
+
+def test_library_continuation_table_matches_the_oracle(tables):
+    """The CUDA library builds its continuation operator with its own
+    generator (Gram-Schmidt and normal equations in 100 digits); both are
+    roundings of the same operator A Q^T (independent of the Gram
+    polynomials' signs)."""
+    import os
+    import re
+    path = os.path.join(os.path.dirname(__file__), "..", "paper_2301_03814_gb300", "csrc",
+                        "swkb_fc_tables.h")
+    txt = open(path).read()
+    body = txt[txt.index("= {") + 3:txt.index("};")]
+    lib = np.array([float(v) for v in re.findall(r"[-+]?\d\.\d+e[-+]\d+", body)])
+    Q, A = tables
+    want = A @ Q.T
+    assert lib.shape == (want.size,)
+    assert np.max(np.abs(lib.reshape(want.shape) - want)) <= 1e-15 * np.max(np.abs(want))

@@ -1,0 +1,137 @@
+"""Patch-wise Fourier-continuation screens (Sec. 2.2) on the GPU, through the
+C ABI, against the continuation oracle (oracle/fc_oracle.py).
+
+Tolerances: FP64 plans max |gpu - oracle| <= 1e-10 of the field's max (same
+arithmetic, different summation order); mixed plans (FP32 rays and sum, FP64
+continuation and DFT) <= 1e-4."""
+import math
+
+import numpy as np
+import pytest
+
+import fc_pins as P
+from paper_2301_03814_gb300 import swkb
+from paper_2301_03814_gb300 import workloads as w
+
+pytestmark = pytest.mark.gpu
+pytest.importorskip("mpmath")
+
+from oracle.fc_oracle import FCOracle  # noqa: E402
+
+FP64_TOL = 1e-10
+MIXED_TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _err(got, want):
+    return float(np.max(np.abs(got - want)) / np.max(np.abs(want)))
+
+
+def lens(n_screens=2, ray_stride=1, P_=3, n_pat=144, n_ov=48, zc=52.0, tilt=6.0, cols=1):
+    H = ((P_ - 1) * (n_pat - n_ov) + n_pat) * P.STEP
+    pb = P.open_problem(n_pat, n_ov, P_, zc, tilt, 5.0, medium=w.f_gaussian(0.01, 0.01, zc=H / 2),
+                        n_screens=n_screens, rk4_steps=8, ray_stride=ray_stride)
+    if cols > 1:
+        # range-dependent: the lens strengthens linearly between two columns
+        prof = pb.profile
+        f2 = w.f_gaussian(0.02, 0.01, zc=H / 2)
+        e2, ez2, ezz2 = f2(prof.nodes())
+        prof = w.Profile(np.array([0.0, 2 * pb.dx]), prof.z0, prof.dz,
+                         np.vstack([prof.eps, e2]), np.vstack([prof.eps_z, ez2]),
+                         np.vstack([prof.eps_zz, ezz2]))
+        pb = pb.with_(profile=prof)
+    return pb
+
+
+CASES = {
+    "lens-3x144": lambda: lens(),
+    "lens-R2": lambda: lens(ray_stride=2, P_=4, n_pat=160, n_ov=48),
+    "lens-1-patch": lambda: lens(P_=1, n_pat=240, n_ov=48, zc=40.0, n_screens=3),
+    "lens-range-dependent": lambda: lens(cols=2, n_screens=3),
+    "homogeneous-6x120": lambda: P.open_problem(120, 40, 6, 90.0, -7.0, 5.0, n_screens=2),
+}
+
+_oracle = {}
+
+
+def oracle_field(name):
+    if name not in _oracle:
+        pb = CASES[name]()
+        _oracle[name] = FCOracle(pb).propagate(pb.u0)
+    return _oracle[name]
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_fp64_matches_oracle(name):
+    pb = CASES[name]()
+    plan = swkb.Plan(pb, precision=swkb.SWKB_FP64)
+    assert plan.info.fc_patches == (pb.n_z - pb.fc_patch) // (pb.fc_patch - pb.fc_overlap) + 1
+    assert plan.info.fc_period_points == pb.fc_patch + 25
+    got = plan.propagate()
+    assert _err(got, oracle_field(name)) <= FP64_TOL
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_mixed_matches_oracle(name):
+    pb = CASES[name]()
+    got = swkb.Plan(pb, precision=swkb.SWKB_MIXED).propagate()
+    assert _err(got, oracle_field(name)) <= MIXED_TOL
+
+
+def test_modes_and_rays_match_the_oracle_mode_set():
+    pb = lens()
+    o = FCOracle(pb)
+    info = swkb.Plan(pb).info
+    assert info.n_max == o.n_max and info.n_ghost == o.G
+    assert info.n_fft == (pb.n_z + 255) // 256 * 256
+    assert info.n_rays_total == info.n_fft // pb.ray_stride + 2 * o.G
+    assert abs(info.period - o.Lp) < 1e-12 * o.Lp
+
+
+def test_snapshots_and_resume_match_one_call():
+    pb = lens(n_screens=4)
+    plan = swkb.Plan(pb, precision=swkb.SWKB_FP64)
+    whole = plan.propagate()
+    snaps = plan.propagate(snapshot_every=2)
+    assert np.array_equal(snaps[-1], whole)
+    half = plan.propagate(n_screens=2)
+    resumed = plan.propagate(u0=half, q0=2, n_screens=2)
+    assert np.array_equal(resumed, whole)
+
+
+def test_homogeneous_against_angular_spectrum():
+    """Physics through the GPU: one screen in eps = 1 against the exact
+    propagator (the oracle's pin, < 2e-6 with 48-point overlaps)."""
+    pb = P.open_problem(144, 48, 3, (144 - 24) * P.STEP, 8.0, 5.0)
+    got = swkb.Plan(pb, precision=swkb.SWKB_FP64).propagate()
+    assert _err(got, P.angular_spectrum(pb.u0, pb.dx)) < 2e-6
+
+
+@pytest.mark.parametrize("kw,msg", [
+    (dict(fc_patch=80, fc_overlap=16, n_z=300), "tile"),        # patches do not tile n_z
+    (dict(fc_patch=30, fc_overlap=16, n_z=272), "tile"),        # ramps would overlap
+    (dict(fc_patch=2100, fc_overlap=64, n_z=2100), "2048"),     # continued period too long
+])
+def test_invalid_layouts_are_refused(kw, msg):
+    pb = P.open_problem(144, 48, 3, 50.0, 0.0, 5.0)
+    n_z = kw.pop("n_z")
+    H = n_z * P.STEP
+    pb = pb.with_(n_z=n_z, z_b=H, u0=np.zeros(n_z, dtype=np.complex128), **kw)
+    with pytest.raises(swkb.SwkbError) as e:
+        swkb.Plan(pb)
+    assert e.value.status == swkb.SWKB_ERR_INVALID_ARG
+    assert msg in str(e.value)
+
+
+def test_absorber_and_planes_are_refused():
+    pb = lens()
+    with pytest.raises(swkb.SwkbError):
+        swkb.Plan(pb.with_(absorber_frac=0.1))
+    with pytest.raises(swkb.SwkbError):
+        swkb.Plan(pb, planes=2)
