@@ -61,12 +61,15 @@ def parse_args():
                     help="fixed launch shapes of the mixed plan (tile_points, ctas_per_sm, "
                          "fft_n1, as the JSON line's \"tiling\" reports them) instead of "
                          "autotuning: a profiler run then times the shapes a plain run chose")
-    ap.add_argument("--case", choices=("plan4", "batch8"), default=None,
+    ap.add_argument("--case", choices=("plan4", "batch8", "open16k", "open131k"), default=None,
                     help="instead of the benchmark, run one small profiling case twice and exit "
                          "(no JSON line): plan4 = 4 screens of the bench workload's mixed plan "
                          "(shapes from --tiling, else autotuned); batch8 = the first 8 "
                          "instances of the uneven batch, 12 screens each, in one persistent "
-                         "launch")
+                         "launch; open16k / open131k = 4 screens of the open lens (patch-wise "
+                         "continuation, mixed) at N_z = 16384 / 131072")
+    ap.add_argument("--no-patchwise", action="store_true",
+                    help="skip the overlapping Fourier-continuation leg (open lens, N_z = 131072)")
     ap.add_argument("--large", action="store_true",
                     help="instead of the benchmark, time the paper-scale range-dependent duct "
                          "and the full uneven batch once (one JSON line; minutes)")
@@ -588,6 +591,118 @@ def paper_scale_measurement(swkb, dev):
                       "run); inputs resident"}
 
 
+def fc_resum_flops_per_term():
+    # Newton-form interpolation of phase and complex amplitude (3 cubics, 21),
+    # exact integer phase + reduction (4), sincos (2), complex multiply-
+    # accumulate (8)
+    return 35
+
+
+def patchwise_measurement(swkb, dev, pk):
+    """The overlapping Fourier-continuation path (Sec. 2.2) on its own
+    workload, the open lens (N_z = 131072, 188 patches of 920 points, 545
+    modes per patch, 100 screens of 5 wavelengths, R = 8): one full mixed
+    propagation timed with CUDA events on the plan's stream (graph captured
+    by a warm-up run), a serialised 10-screen kernel breakdown with the
+    dominant kernel's roofline, 10 screens in FP64 (rel-L2 against mixed),
+    and the same problem family at N_z = 8192 / 16384 / 32768 through the
+    patch-wise and the periodic path (ms per screen; FP64 fields compared
+    at 8192 and 16384)."""
+    import torch
+    from paper_2301_03814_gb300 import workloads as w
+    stream = torch.cuda.Stream(device=dev)
+
+    def run(plan, u0, n):
+        d_in = torch.from_numpy(u0).to(dev)
+        d_out = torch.empty_like(d_in)
+        plan.propagate_device(d_in.data_ptr(), d_out.data_ptr(), n_screens=n)   # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.propagate_device(d_in.data_ptr(), d_out.data_ptr(), n_screens=n)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), d_out.cpu().numpy()
+
+    pb = w.config_open_lens()
+    plan = swkb.Plan(pb, swkb.SWKB_MIXED, stream=stream.cuda_stream, device=dev.index)
+    info = plan.info
+    ms, field = run(plan, pb.u0, pb.n_screens)
+    plan.set_timing(True, 1, True)
+    d_in = torch.from_numpy(pb.u0).to(dev)
+    d_out = torch.empty_like(d_in)
+    plan.propagate_device(d_in.data_ptr(), d_out.data_ptr(), n_screens=10)
+    torch.cuda.synchronize()
+    st = plan.stats()
+    plan.set_timing(0, 1, False)
+    _, mixed10 = run(plan, pb.u0, 10)
+    plan.close()
+    plan64 = swkb.Plan(pb, swkb.SWKB_FP64, stream=stream.cuda_stream, device=dev.index)
+    ms64, fp64_10 = run(plan64, pb.u0, 10)
+    plan64.close()
+    kms = {k: v / 10 for k, v in st["kernel_ms"].items()}
+    share = {k: round(v / max(sum(kms.values()), 1e-30), 4) for k, v in kms.items()}
+    dom = max(("march", "resum", "fft"), key=lambda k: kms[k])
+    rays = info.n_modes * info.n_rays_total
+    terms = info.n_modes * info.n_fft
+    roof = None
+    if st["kernel_timed"][dom]:
+        per = st["kernel_ms"][dom] / 1e3 / st["kernel_timed"][dom]
+        if dom == "march":
+            work = march_flops_per_ray(pb) * rays
+            note = f"{rays} rays x {march_flops_per_ray(pb)} flops (4 N_t (30 + 45 + sqrt + div))"
+        elif dom == "resum":
+            work = fc_resum_flops_per_term() * terms
+            note = f"{terms} terms (modes x points) x {fc_resum_flops_per_term()} flops"
+        else:
+            work = 8 * info.fc_patches * info.n_modes * info.fc_period_points
+            note = "patches x modes x N_p complex multiply-adds (8 flops)"
+        ach = work / per / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": pk["fp32_tflops"],
+                "unit": "TFLOP/s", "frac": ach / pk["fp32_tflops"], "launch_ms": per * 1e3,
+                "work_per_launch": work, "work_unit": note, "peak_source": pk["fp32_src"]}
+    resum_mufu = None
+    if st["kernel_timed"]["resum"]:
+        per = st["kernel_ms"]["resum"] / 1e3 / st["kernel_timed"]["resum"]
+        ach = MUFU_PER_TERM * terms / per / 1e12
+        resum_mufu = {"bound": "mufu", "achieved": ach, "peak": pk["mufu_tops"], "unit": "Tops/s",
+                      "frac": ach / pk["mufu_tops"], "launch_ms": per * 1e3,
+                      "peak_source": pk["mufu_src"]}
+    out = {"workload": pb.name, "n_z": pb.n_z, "patches": info.fc_patches,
+           "patch_points": pb.fc_patch, "overlap_points": pb.fc_overlap,
+           "continued_period_points": info.fc_period_points, "modes_per_patch": info.n_modes,
+           "ray_stride": pb.ray_stride, "rays_per_mode": info.n_rays_total,
+           "screens": pb.n_screens, "ms": ms,
+           "screen_points_per_s": pb.n_z * pb.n_screens / (ms / 1e3),
+           "finite": bool(np.isfinite(field).all()),
+           "fp64_10_screens_ms": ms64, "fp64_screen_points_per_s": pb.n_z * 10 / (ms64 / 1e3),
+           "mixed_vs_fp64_rel_l2_10_screens": rel_l2(mixed10, fp64_10),
+           "kernel_ms_per_screen": kms, "kernel_share": share, "roofline": roof,
+           "resum_mufu_roofline": resum_mufu,
+           "timing": "CUDA events on the plan's stream around one full propagation (graph "
+                     "captured by a warm-up run); inputs resident; breakdown serialised"}
+    cmp = []
+    for n_z, npat, nov in ((8192, 910, 248), (16384, 904, 259), (32768, 902, 224)):
+        small = w.config_open_lens(n_z=n_z, fc_patch=npat, fc_overlap=nov, n_screens=10)
+        per_pb = small.with_(bc=w.BC_PERIODIC)
+        row = {"n_z": n_z}
+        for name, q in (("patchwise", small), ("periodic", per_pb)):
+            pl = swkb.Plan(q, swkb.SWKB_MIXED, stream=stream.cuda_stream, device=dev.index)
+            t, _ = run(pl, small.u0, 10)
+            row[f"{name}_modes"] = pl.info.n_modes
+            row[f"{name}_ms_per_screen"] = t / 10
+            pl.close()
+        if n_z <= 16384:
+            f = {}
+            for name, q in (("patchwise", small), ("periodic", per_pb)):
+                pl = swkb.Plan(q, swkb.SWKB_FP64, stream=stream.cuda_stream, device=dev.index)
+                _, f[name] = run(pl, small.u0, 10)
+                pl.close()
+            row["fp64_patchwise_vs_periodic_rel_l2"] = rel_l2(f["patchwise"], f["periodic"])
+        cmp.append(row)
+    out["vs_periodic"] = cmp
+    return out
+
+
 def sov_measurement(swkb, dev, with_oracle):
     """The separation-of-variables reference (Sec. 3.1) on the GPU: FP64
     Galerkin matrices, batched Jacobi eigen-solve, projection and advance,
@@ -861,6 +976,8 @@ def run_ours(args, world, rank, local):
         line["sov_reference"] = sov_measurement(swkb, dev, not args.no_cpu_baseline)
     if world == 1 and not args.no_paper_scale:
         line["paper_scale"] = paper_scale_measurement(swkb, dev)
+    if world == 1 and not args.no_patchwise:
+        line["patchwise"] = patchwise_measurement(swkb, dev, pk)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(pb)
     print(json.dumps(line), flush=True)
@@ -927,6 +1044,15 @@ def run_case(args):
         pb = workload().with_(n_screens=4)
         fixed = tuple(int(v) for v in args.tiling.split(",")) if args.tiling else None
         plan = swkb.Plan(pb, swkb.SWKB_MIXED, autotune=fixed is None, tiling=fixed)
+        u = torch.from_numpy(pb.u0).cuda()
+        out = torch.empty_like(u)
+        for _ in range(2):
+            plan.propagate_device(u.data_ptr(), out.data_ptr())
+    elif args.case in ("open16k", "open131k"):
+        # the patch-wise continuation path: open lens, 4 screens, mixed
+        pb = (w.config_open_lens(n_z=16384, fc_patch=904, fc_overlap=259)
+              if args.case == "open16k" else w.config_open_lens()).with_(n_screens=4)
+        plan = swkb.Plan(pb, swkb.SWKB_MIXED)
         u = torch.from_numpy(pb.u0).cuda()
         out = torch.empty_like(u)
         for _ in range(2):

@@ -144,14 +144,14 @@ typedef struct {
   int32_t fft_n1;         /* DFT split N = fft_n1 * (N / fft_n1)              */
   /* SWKB_BC_OPEN only (ignored otherwise).  Patch p holds the grid points
      p (fc_patch - fc_overlap) .. p (fc_patch - fc_overlap) + fc_patch - 1;
-     the patches must tile the n_z points exactly, 2 <= fc_overlap,
-     2 fc_overlap <= fc_patch and fc_patch + 25 <= 2048.  Each patch's
-     samples are continued by FC-Gram (5 matching points, 25 continuation
-     points) to a sequence of N_p = fc_patch + 25 points whose DFT gives the
-     patch's modes (kappa_n = 2 pi n / (k N_p dz), |n| <= floor(sin(theta_max)
-     N_p dz / lambda) or n_max); the partition of unity S^p rises and falls
-     over fc_overlap points (a C-infinity step), also at the interval's two
-     ends; every ray of mode n launched at z_j carries
+     the patches must tile the n_z points exactly, with 2 <= fc_overlap,
+     2 fc_overlap <= fc_patch, 16 <= fc_patch and fc_patch + 25 <= 2048.
+     Each patch's samples are continued by FC-Gram (5 matching points, 25
+     continuation points) to a sequence of N_p = fc_patch + 25 points whose
+     DFT gives the patch's modes (kappa_n = 2 pi n / (k N_p dz), |n| <=
+     floor(sin(theta_max) N_p dz / lambda) or n_max); the partition of unity
+     S^p rises and falls over fc_overlap points (a C-infinity step), also at
+     the interval's two ends; every ray of mode n launched at z_j carries
      sum_p S^p(z_j) w_n^p / N_p.  No absorber, no inner planes, no autotune;
      swkb_debug_screen and the batch kernel refuse these plans. */
   int32_t fc_patch;

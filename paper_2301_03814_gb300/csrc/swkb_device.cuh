@@ -631,9 +631,13 @@ __device__ __forceinline__ void bracket_body(const BracketArgs<T>& p, int bx, in
   if (st) atomicOr(p.status, st);
 }
 
+// Rows of landing pairs beyond the grid's y extent (65535) are taken in
+// strides of gridDim.y.
 template <typename T>
 __global__ void __launch_bounds__(256) k_bracket(const BracketArgs<T> p) {
-  bracket_body<T, LD_PLAIN>(p, blockIdx.x, blockIdx.y, threadIdx.x);
+  const int rows = (p.NRT - 1 + BRACKET_RUN - 1) / BRACKET_RUN;
+  for (int by = blockIdx.y; by < rows; by += gridDim.y)
+    bracket_body<T, LD_PLAIN>(p, blockIdx.x, by, threadIdx.x);
 }
 
 // ----------------------------------------------------------------------------

@@ -8,9 +8,9 @@
 //               continuation to N_p = n_pat + C points, and the kept modes of
 //               that sequence's DFT, w_n / N_p, rotated to the interval's
 //               origin (exp(-2 pi i n s_p / N_p)) and carried over the screen
-//               (exp(i k dx Pbar_n)): cf[p][n].  FP64 throughout (the
-//               continuation operator's entries reach 3e3, so its
-//               cancellations need FP64 even in mixed plans).
+//               (exp(i k dx Pbar_n)): cf[p][n].  The continuation runs in
+//               FP64 in every plan (the operator's entries reach 3e3, so its
+//               cancellations need FP64); the DFT sums in the plan's type.
 //   k_fc_resum  the interpolation fused with the modal sum, as the periodic
 //               resummation, except that a ray's amplitude is complex: ray
 //               (n, j) carries a_j (S^{p0}(z_j) cf[p0][n] + S^{p0+1}(z_j)
@@ -27,55 +27,84 @@ namespace swkb {
 namespace {
 
 constexpr int FC_MODES_THREADS = 256;
+constexpr int FC_MODES_PER_CTA = 64;   // 8 warps x 8 modes
 constexpr int FC_WARPS = 4;
-constexpr int FC_CF = 16;   // X_w, X_{w+1}, phase b0..b3, Re a r0..r3, Im a i0..i3, 2 pad
+constexpr int FC_PF = 2;    // rounds of 32 rays prefetched one mode ahead
+// Row of interval w: X_w, X_{w+1}, phase b0..b3, Re a r0..r3, Im a i0..i3.
+// 14 values accessed as 7 pairs: at a 56-byte (FP32) row stride the 16
+// lanes of a half-warp touch 32 distinct banks.
+constexpr int FC_CF = 14;
+
+// x mod Np for x < 2^32 with magic = floor(2^32 / Np): the quotient
+// estimate is floor(x / Np) or one less, so one correction finishes it.
+__device__ __forceinline__ unsigned mod_np(unsigned x, unsigned Np, unsigned magic) {
+  unsigned r = x - __umulhi(x, magic) * Np;
+  return r >= Np ? r - Np : r;
+}
 
 template <typename T>
 __host__ __device__ inline int fc_warp_bytes(int wcap) {
   return ((FC_CF + 4) * wcap * (int)sizeof(T) + 15) & ~15;
 }
 
+// CTA (patch blockIdx.x, mode block blockIdx.y): the continuation in FP64,
+// then the DFT of the FC_MODES_PER_CTA modes of the block in T (a mixed plan
+// sums in FP32: exact twiddle indices, FP32 twiddles and samples).
 template <typename T>
 __global__ void __launch_bounds__(FC_MODES_THREADS) k_fc_modes(const FcModesArgs<T> p) {
   using V = typename C2<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2* e = reinterpret_cast<double2*>(smem_raw);   // [N_p] the continued sequence
-  double2* tw = e + p.Np;                              // [N_p] exp(-2 pi i k / N_p)
+  V* e = reinterpret_cast<V*>(smem_raw);    // [N_p] the continued sequence
+  V* tw = e + p.Np;                         // [N_p] exp(-2 pi i k / N_p)
+  __shared__ double2 ends[2 * FC_D];        // the d samples at each end, FP64
   const int pt = blockIdx.x;
   const long long s0 = (long long)pt * p.stride;
   for (int k = threadIdx.x; k < p.n_pat; k += blockDim.x) {
     const V v = p.u[s0 + k];
-    e[k] = make_double2((double)v.x, (double)v.y);
+    e[k] = v;
+    if (k < FC_D) ends[FC_D + k] = make_double2((double)v.x, (double)v.y);
+    if (k >= p.n_pat - FC_D) ends[k - (p.n_pat - FC_D)] = make_double2((double)v.x, (double)v.y);
   }
-  for (int k = threadIdx.x; k < p.Np; k += blockDim.x) tw[k] = p.tw[k];
+  for (int k = threadIdx.x; k < p.Np; k += blockDim.x) {
+    const double2 w = p.tw[k];
+    V v;
+    v.x = (T)w.x;
+    v.y = (T)w.y;
+    tw[k] = v;
+  }
   __syncthreads();
   if (threadIdx.x < FC_C) {
-    // value t past the right end: the right end's d samples through row t;
-    // the same value counted backwards from the left end is C - t steps
-    // before sample 0: the left end read backwards through row C - 1 - t
+    // value t past the right end: the right end's d samples (ends[0 .. d-1])
+    // through row t; the same value counted backwards from the left end is
+    // C - t steps before sample 0: the left end read backwards (sample
+    // d - 1 - i = ends[2 d - 1 - i]) through row C - 1 - t
     const int t = threadIdx.x;
     double ar = 0.0, ai = 0.0;
     for (int i = 0; i < FC_D; ++i) {
       const double cr = p.cont[t * FC_D + i];
       const double cl = p.cont[(FC_C - 1 - t) * FC_D + i];
-      const double2 fr = e[p.n_pat - FC_D + i];
-      const double2 fl = e[FC_D - 1 - i];
+      const double2 fr = ends[i];
+      const double2 fl = ends[2 * FC_D - 1 - i];
       ar += cr * fr.x + cl * fl.x;
       ai += cr * fr.y + cl * fl.y;
     }
-    e[p.n_pat + t] = make_double2(ar, ai);
+    V v;
+    v.x = (T)ar;
+    v.y = (T)ai;
+    e[p.n_pat + t] = v;
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned Np = (unsigned)p.Np;
-  for (int i = warp; i < p.M; i += FC_MODES_THREADS / 32) {
-    const int n = i - p.n_max;
-    const unsigned nn = (unsigned)(((n % p.Np) + p.Np) % p.Np);
-    const unsigned step = (unsigned)(((unsigned long long)nn * 32u) % Np);
-    unsigned idx = (unsigned)(((unsigned long long)nn * (unsigned)lane) % Np);
-    double sr = 0.0, si = 0.0;
+  const int i_end = min(p.M, (int)(blockIdx.y + 1) * FC_MODES_PER_CTA);
+  for (int i = blockIdx.y * FC_MODES_PER_CTA + warp; i < i_end; i += FC_MODES_THREADS / 32) {
+    const int n = i - p.n_max;   // |n| < Np / 2
+    const unsigned nn = (unsigned)(n < 0 ? n + p.Np : n);
+    const unsigned step = mod_np(nn * 32u, Np, p.np_magic);
+    unsigned idx = mod_np(nn * (unsigned)lane, Np, p.np_magic);
+    T sr = T(0), si = T(0);
     for (int k = lane; k < p.Np; k += 32) {
-      const double2 v = e[k], w = tw[idx];
+      const V v = e[k], w = tw[idx];
       sr += v.x * w.x - v.y * w.y;
       si += v.x * w.y + v.y * w.x;
       idx += step;
@@ -87,11 +116,13 @@ __global__ void __launch_bounds__(FC_MODES_THREADS) k_fc_modes(const FcModesArgs
       si += __shfl_xor_sync(0xffffffffu, si, o);
     }
     if (lane == 0) {
-      const double2 rot = tw[(unsigned)(((unsigned long long)nn * (unsigned long long)s0) % Np)];
+      // nn s0 < 2^11 2^20: no overflow
+      const double2 rot = p.tw[mod_np(nn * (unsigned)s0, Np, p.np_magic)];
       const V ep = p.ephi[i];
       const double er = (double)ep.x, ei = (double)ep.y;
       // (sr + i si) rot exp(i phi) / N_p
-      const double xr = sr * rot.x - si * rot.y, xi = sr * rot.y + si * rot.x;
+      const double xr = (double)sr * rot.x - (double)si * rot.y;
+      const double xi = (double)sr * rot.y + (double)si * rot.x;
       V c;
       c.x = (T)((xr * er - xi * ei) * p.inv_Np);
       c.y = (T)((xr * ei + xi * er) * p.inv_Np);
@@ -100,25 +131,18 @@ __global__ void __launch_bounds__(FC_MODES_THREADS) k_fc_modes(const FcModesArgs
   }
 }
 
-__device__ __forceinline__ void store_row(float* r, float X1, float X2, float b0, float b1,
-                                          float b2, float b3, float r0, float r1, float r2,
-                                          float r3, float i0, float i1, float i2, float i3) {
-  *reinterpret_cast<float4*>(r) = make_float4(X1, X2, b0, b1);
-  *reinterpret_cast<float4*>(r + 4) = make_float4(b2, b3, r0, r1);
-  *reinterpret_cast<float4*>(r + 8) = make_float4(r2, r3, i0, i1);
-  *reinterpret_cast<float4*>(r + 12) = make_float4(i2, i3, 0.f, 0.f);
-}
-__device__ __forceinline__ void store_row(double* r, double X1, double X2, double b0, double b1,
-                                          double b2, double b3, double r0, double r1, double r2,
-                                          double r3, double i0, double i1, double i2,
-                                          double i3) {
-  *reinterpret_cast<double2*>(r) = make_double2(X1, X2);
-  *reinterpret_cast<double2*>(r + 2) = make_double2(b0, b1);
-  *reinterpret_cast<double2*>(r + 4) = make_double2(b2, b3);
-  *reinterpret_cast<double2*>(r + 6) = make_double2(r0, r1);
-  *reinterpret_cast<double2*>(r + 8) = make_double2(r2, r3);
-  *reinterpret_cast<double2*>(r + 10) = make_double2(i0, i1);
-  *reinterpret_cast<double2*>(r + 12) = make_double2(i2, i3);
+template <typename T>
+__device__ __forceinline__ void store_row(T* r, T X1, T X2, T b0, T b1, T b2, T b3, T r0, T r1,
+                                          T r2, T r3, T i0, T i1, T i2, T i3) {
+  using V = typename C2<T>::type;
+  V* q = reinterpret_cast<V*>(r);
+  q[0] = V{X1, X2};
+  q[1] = V{b0, b1};
+  q[2] = V{b2, b3};
+  q[3] = V{r0, r1};
+  q[4] = V{r2, r3};
+  q[5] = V{i0, i1};
+  q[6] = V{i2, i3};
 }
 
 template <typename T>
@@ -128,24 +152,10 @@ struct Row {
 
 template <typename T>
 __device__ __forceinline__ Row<T> load_row(const T* r) {
-  Row<T> o;
-  if constexpr (sizeof(T) == 4) {
-    const float4 a = *reinterpret_cast<const float4*>(r);
-    const float4 b = *reinterpret_cast<const float4*>(r + 4);
-    const float4 c = *reinterpret_cast<const float4*>(r + 8);
-    const float2 d = *reinterpret_cast<const float2*>(r + 12);
-    o = Row<T>{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w, d.x, d.y};
-  } else {
-    const double2 a = *reinterpret_cast<const double2*>(r);
-    const double2 b = *reinterpret_cast<const double2*>(r + 2);
-    const double2 c = *reinterpret_cast<const double2*>(r + 4);
-    const double2 d = *reinterpret_cast<const double2*>(r + 6);
-    const double2 f = *reinterpret_cast<const double2*>(r + 8);
-    const double2 g = *reinterpret_cast<const double2*>(r + 10);
-    const double2 h = *reinterpret_cast<const double2*>(r + 12);
-    o = Row<T>{a.x, a.y, b.x, b.y, c.x, c.y, d.x, d.y, f.x, f.y, g.x, g.y, h.x, h.y};
-  }
-  return o;
+  using V = typename C2<T>::type;
+  const V* q = reinterpret_cast<const V*>(r);
+  const V a = q[0], b = q[1], c = q[2], d = q[3], e = q[4], f = q[5], g = q[6];
+  return Row<T>{a.x, a.y, b.x, b.y, c.x, c.y, d.x, d.y, e.x, e.y, f.x, f.y, g.x, g.y};
 }
 
 // One CTA: tile blk % n_tiles (TM = 32 PW points), mode group blk / n_tiles;
@@ -173,34 +183,93 @@ __global__ void __launch_bounds__(FC_WARPS * 32) k_fc_resum(const FcResumArgs<T>
 #pragma unroll
   for (int q = 0; q < PW; ++q) { accr[q] = T(0); acci[q] = T(0); }
 
-  for (int i = i0 + warp; i < i1; i += FC_WARPS) {
-    const int jl = p.jlo[bchk((long long)tile * p.M + i, njlo, st)];
-    const int jh = p.jlo[bchk((long long)(tile + 1) * p.M + i, njlo, st)];
-    // a table left inconsistent by a failed screen (flagged by the bracket
-    // kernel) must not send the reads out of [0, NRT)
-    if (jl < 1 || jh < jl || jh > p.NRT - 3) continue;
+  // ray j of mode i: landing offset, phase and the complex amplitude
+  // a_j (S^{p0}(z_j) cf[p0][i] + S^{p0+1}(z_j) cf[p0+1][i])
+  auto fetch = [&](int i, int j, T& d, T& ph, T& ar, T& ai) {
+    const long long o = bchk((long long)j * p.M + i, nrays, st);
+    d = ld<LD_NC>(p.d + o);
+    ph = ld<LD_NC>(p.ph + o);
+    const T a = ld<LD_NC>(p.a + o);
+    const int p0 = p.win_p[j];
+    const V sw = p.win_s[j];
+    const V c0 = p.cf[bchk((long long)p0 * p.M + i, (long long)p.P * p.M, st)];
+    T cr = sw.x * c0.x, ci = sw.x * c0.y;
+    if (p0 + 1 < p.P) {
+      const V c1 = p.cf[(long long)(p0 + 1) * p.M + i];
+      cr += sw.y * c1.x;
+      ci += sw.y * c1.y;
+    }
+    ar = a * cr;
+    ai = a * ci;
+  };
+  auto head = [&](int i, int& jl, int& jh) {
+    jl = -1;
+    jh = -1;
+    if (i >= i1) return;
+    jl = p.jlo[bchk((long long)tile * p.M + i, njlo, st)];
+    jh = p.jlo[bchk((long long)(tile + 1) * p.M + i, njlo, st)];
+  };
+  // a table left inconsistent by a failed screen (flagged by the bracket
+  // kernel) must not send the reads out of [0, NRT); a window beyond the
+  // tile's capacity means rays compressed beyond it (flagged here)
+  auto head_ok = [&](int i, int jl, int jh) {
+    if (i >= i1 || jl < 1 || jh < jl || jh > p.NRT - 3) return false;
+    if (jh - jl + 4 > wcap) {
+      st |= ST_CAUSTIC;
+      return false;
+    }
+    return true;
+  };
+  // the next mode's first FC_PF rounds of 32 rays are loaded into registers
+  // while the current mode is summed
+  T pd[FC_PF], pph[FC_PF], par[FC_PF], pai[FC_PF];
+  auto prefetch = [&](int i, int jl, int jh) {
     const int W = jh - jl + 4;
-    if (W > wcap) { st |= ST_CAUSTIC; continue; }
+#pragma unroll
+    for (int r = 0; r < FC_PF; ++r) {
+      const int w = lane + 32 * r;
+      if (w < W) fetch(i, jl - 1 + w, pd[r], pph[r], par[r], pai[r]);
+    }
+  };
+
+  int i = i0 + warp;
+  int jl_c, jh_c, jl_n, jh_n;
+  head(i, jl_c, jh_c);
+  head(i + FC_WARPS, jl_n, jh_n);
+  bool ok_c = head_ok(i, jl_c, jh_c);
+  if (ok_c) prefetch(i, jl_c, jh_c);
+  for (; i < i1; i += FC_WARPS) {
+    const bool ok = ok_c;
+    const int jl = jl_c, jh = jh_c;
+    const int W = jh - jl + 4;
     const int jb = jl - 1;
     __syncwarp();
-    for (int w = lane; w < W; w += 32) {
-      const int j = jb + w;
-      const long long o = bchk((long long)j * p.M + i, nrays, st);
-      s_X[w] = T((j - p.G) * p.R - m0) + ld<LD_NC>(p.d + o);
-      s_ph[w] = ld<LD_NC>(p.ph + o);
-      const T a = ld<LD_NC>(p.a + o);
-      const int p0 = p.win_p[j];
-      const V s = p.win_s[j];
-      const V c0 = p.cf[bchk((long long)p0 * p.M + i, (long long)p.P * p.M, st)];
-      T cr = s.x * c0.x, ci = s.x * c0.y;
-      if (p0 + 1 < p.P) {
-        const V c1 = p.cf[(long long)(p0 + 1) * p.M + i];
-        cr += s.y * c1.x;
-        ci += s.y * c1.y;
+    if (ok) {
+#pragma unroll
+      for (int r = 0; r < FC_PF; ++r) {
+        const int w = lane + 32 * r;
+        if (w < W) {
+          s_X[w] = T((jb + w - p.G) * p.R - m0) + pd[r];
+          s_ph[w] = pph[r];
+          s_ar[w] = par[r];
+          s_ai[w] = pai[r];
+        }
       }
-      s_ar[w] = a * cr;
-      s_ai[w] = a * ci;
+      for (int w = lane + 32 * FC_PF; w < W; w += 32) {
+        T d, ph, ar, ai;
+        fetch(i, jb + w, d, ph, ar, ai);
+        s_X[w] = T((jb + w - p.G) * p.R - m0) + d;
+        s_ph[w] = ph;
+        s_ar[w] = ar;
+        s_ai[w] = ai;
+      }
     }
+    jl_c = jl_n;
+    jh_c = jh_n;
+    ok_c = head_ok(i + FC_WARPS, jl_c, jh_c);
+    if (ok_c) prefetch(i + FC_WARPS, jl_c, jh_c);
+    head(i + 2 * FC_WARPS, jl_n, jh_n);
+    if (!ok) continue;
     __syncwarp();
     for (int w = 1 + lane; w <= W - 3; w += 32) {
       const T X0 = s_X[w - 1], X1 = s_X[w], X2 = s_X[w + 1], X3 = s_X[w + 2];
@@ -228,9 +297,10 @@ __global__ void __launch_bounds__(FC_WARPS * 32) k_fc_resum(const FcResumArgs<T>
     while (w > 1 && s_X[w] > xv0) --w;
     while (w < W - 3 && s_X[w + 1] <= xv0) ++w;
     Row<T> r = load_row<T>(s_cf + FC_CF * w);
-    const int n = i - p.n_max;
-    const unsigned nn = (unsigned)(((n % p.Np) + p.Np) % p.Np);
-    unsigned nm = (unsigned)(((unsigned long long)nn * (unsigned long long)(m0 + x0)) % Np);
+    const int n = i - p.n_max;   // |n| < Np / 2
+    const unsigned nn = (unsigned)(n < 0 ? n + p.Np : n);
+    // nn (m0 + x0) < 2^11 2^20: no overflow
+    unsigned nm = mod_np(nn * (unsigned)(m0 + x0), Np, p.np_magic);
 #pragma unroll
     for (int q = 0; q < PW; ++q) {
       const T xv = xv0 + T(q);
@@ -296,7 +366,7 @@ size_t fc_resum_smem_bytes(int wcap, int tile_points) {
 
 template <typename T>
 size_t fc_modes_smem_bytes(int Np) {
-  return 2 * (size_t)Np * sizeof(double2);
+  return 2 * (size_t)Np * sizeof(typename C2<T>::type);
 }
 
 template <typename T>
@@ -316,7 +386,8 @@ cudaError_t prepare_fc_kernels(int resum_smem, int modes_smem) {
 
 template <typename T>
 cudaError_t launch_fc_modes(const FcModesArgs<T>& a, cudaStream_t s) {
-  k_fc_modes<T><<<a.P, FC_MODES_THREADS, fc_modes_smem_bytes<T>(a.Np), s>>>(a);
+  const dim3 grid(a.P, (a.M + FC_MODES_PER_CTA - 1) / FC_MODES_PER_CTA);
+  k_fc_modes<T><<<grid, FC_MODES_THREADS, fc_modes_smem_bytes<T>(a.Np), s>>>(a);
   return cudaGetLastError();
 }
 

@@ -149,6 +149,7 @@ struct FcModesArgs {
   const double2* tw;                 // [Np] exp(-2 pi i k / Np)
   const typename C2<T>::type* ephi;  // [M] exp(i k dx Pbar_n)
   double inv_Np;
+  unsigned np_magic;                 // floor(2^32 / Np)
   typename C2<T>::type* cf;          // [P][M] out: rotated, carried mode coefficients
 };
 
@@ -162,6 +163,7 @@ struct FcResumArgs {
   const int* win_p;                  // [NRT] first patch with a non-zero weight at ray j
   const typename C2<T>::type* win_s; // [NRT] (S^{p0}, S^{p0+1}) at ray j
   int M, NRT, G, R, N, TM, n_tiles, n_groups, modes_per_group, n_max, wcap, Np, P;
+  unsigned np_magic;                 // floor(2^32 / Np)
   typename C2<T>::type* part;        // [n_groups][N]
   unsigned* status;
 };

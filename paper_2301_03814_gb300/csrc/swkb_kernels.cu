@@ -104,7 +104,8 @@ cudaError_t launch_march<float>(const MarchArgs<float>& a, bool multi_column, cu
 
 template <typename T>
 cudaError_t launch_bracket(const BracketArgs<T>& a, cudaStream_t s) {
-  dim3 grid((a.Mr + 255) / 256, (a.NRT - 1 + BRACKET_RUN - 1) / BRACKET_RUN);
+  const int rows = (a.NRT - 1 + BRACKET_RUN - 1) / BRACKET_RUN;
+  dim3 grid((a.Mr + 255) / 256, rows < 65535 ? rows : 65535);
   return launch_k(k_bracket<T>, grid, dim3(256), 0, s, a);
 }
 

@@ -781,6 +781,7 @@ FcModesArgs<T> fc_modes_args(const swkb_plan* p) {
   f.tw = (const double2*)p->fc_tw;
   f.ephi = (const V*)p->ephi_d;
   f.inv_Np = 1.0 / p->fc_Np;
+  f.np_magic = (unsigned)((1ULL << 32) / (unsigned long long)p->fc_Np);
   f.cf = (V*)p->fc_cf;
   return f;
 }
@@ -797,6 +798,7 @@ FcResumArgs<T> fc_resum_args(const swkb_plan* p, const T* d, const T* ph, const 
   r.M = p->M; r.NRT = p->NRT; r.G = p->G; r.R = p->R; r.N = p->N; r.TM = p->TM;
   r.n_tiles = p->n_tiles; r.n_groups = p->n_groups; r.modes_per_group = p->modes_per_group;
   r.n_max = p->n_max; r.wcap = p->wcap; r.Np = p->fc_Np; r.P = p->fc_P;
+  r.np_magic = (unsigned)((1ULL << 32) / (unsigned long long)p->fc_Np);
   r.part = (V*)p->part; r.status = p->status;
   return r;
 }
@@ -1442,11 +1444,11 @@ swkb_status configure(swkb_plan* p, const swkb_profile* prof, double k, const sw
     p->fc_stride = p->fc_pat - p->fc_ov;
     if (n_z < 64 || n_z > (1 << 20) - 256)
       return fail(SWKB_ERR_INVALID_ARG, "n_z %d must be in [64, 2^20 - 256]", n_z);
-    if (p->fc_ov < 2 || p->fc_pat < 2 * p->fc_ov || p->fc_pat > n_z ||
+    if (p->fc_ov < 2 || p->fc_pat < 2 * p->fc_ov || p->fc_pat < 16 || p->fc_pat > n_z ||
         (n_z - p->fc_pat) % p->fc_stride)
       return fail(SWKB_ERR_INVALID_ARG,
                   "patches (fc_patch %d, fc_overlap %d) must satisfy 2 <= fc_overlap, "
-                  "2 fc_overlap <= fc_patch <= n_z and tile n_z = %d exactly",
+                  "2 fc_overlap <= fc_patch, 16 <= fc_patch <= n_z and tile n_z = %d exactly",
                   p->fc_pat, p->fc_ov, n_z);
     p->fc_Np = p->fc_pat + FC_CONT_ROWS;
     if (p->fc_Np > 2048)

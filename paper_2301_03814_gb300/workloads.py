@@ -398,6 +398,42 @@ def config_range_dependent_duct(seed=3, height=500.0, n_z=131072, range_m=100_00
                    0.2, meta={"z_t0": z_t0, "g_d": g_d, "sign": sgn, "seed": seed})
 
 
+def config_open_lens(n_z=131072, fc_patch=920, fc_overlap=224, seed=5, n_screens=100,
+                     dx=5.0, n_beams=8, a=0.002, theta_max_deg=60.0, ray_stride=8,
+                     rk4_steps=8, dzp=0.0625):
+    """Open (non-periodic) interval for the patch-wise continuation method:
+    unit wavelength, three grid points per wavelength (N_z = 131072: 43 690
+    wavelengths, 188 patches of 920 points sharing 224), a broad Gaussian
+    lens eps = 1 + a exp(-((z - H/2) / (H/6))^2), and n_beams seeded Gaussian
+    beams (waists 3-10 wavelengths, tilts within +-20 deg) in the middle 70 %
+    of the interval, so that the field vanishes near both ends over the
+    range; screens of dx = 5 wavelengths."""
+    rng = np.random.default_rng(seed)
+    k = 2.0 * math.pi
+    h = 1.0 / 3.0
+    H = n_z * h
+    # launch ghosts and the rays' reach beyond both ends
+    margin = 3.0 * dx * math.tan(math.radians(theta_max_deg)) + 6.0 * ray_stride * h + 4.0
+    z0 = -margin
+    n_p = int(math.ceil((H + 2.0 * margin) / dzp)) + 1
+    zc, wl = H / 2, H / 6
+
+    def lens(z):
+        y = (z - zc) / wl
+        g = a * np.exp(-y * y)
+        return 1.0 + g, -2.0 * y / wl * g, (4.0 * y * y - 2.0) / (wl * wl) * g
+    prof = _table([0.0], z0, dzp, n_p, [lens])
+    z = h * np.arange(n_z)
+    u0 = np.zeros(n_z, dtype=np.complex128)
+    for _ in range(n_beams):
+        c = float(rng.uniform(0.15, 0.85)) * H
+        u0 += gaussian_beam(z, k, c, float(rng.uniform(3.0, 10.0)),
+                            math.radians(float(rng.uniform(-20.0, 20.0))))
+    return Problem(f"open-lens-{n_z}", k, 0.0, H, n_z, BC_OPEN, 0.0, dx, n_screens, prof, u0,
+                   math.radians(theta_max_deg), ray_stride, rk4_steps, 0.0,
+                   fc_patch=fc_patch, fc_overlap=fc_overlap, meta={"seed": seed, "a": a})
+
+
 def random_request(rng, n_z_range=(1 << 12, 1 << 16), range_km=(5.0, 50.0), screens_per_km=20,
                    dzp=0.05):
     """One instance of the uneven batch / served stream: frequency U(1, 10)

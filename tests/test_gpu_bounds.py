@@ -1,9 +1,10 @@
 """The bounds-checked build (libswkb_checked.so, compiled with
 -DSWKB_BOUNDS_CHECK) in place of a memory sanitizer: in the march, bracket
 and resummation kernels every checked index is compared with its buffer, and
-a violation is clamped and reported as an error.  The parity cases run through
-it (in a subprocess, as the library is chosen when it is loaded) without an
-error and give the plain build's fields."""
+a violation is clamped and reported as an error.  The parity cases (and the
+patch-wise continuation path's resummation) run through it (in a subprocess,
+as the library is chosen when it is loaded) without an error and give the
+plain build's fields."""
 import os
 import subprocess
 import sys
@@ -44,6 +45,13 @@ CASES = textwrap.dedent('''
     res["paper_scale"] = swkb.Plan(w.config_range_dependent_duct(n_screens=3, range_m=150.0,
                                                                  col_every_m=50.0),
                                    M).propagate()
+    # patch-wise continuation (open interval): ragged tail past the last
+    # patch, ray strides 1 and 8, both precisions
+    opn = w.config_open_lens(n_z=8192, fc_patch=910, fc_overlap=248, n_screens=2)
+    res["open_mixed"] = swkb.Plan(opn, M).propagate()
+    res["open_fp64_R1"] = swkb.Plan(w.config_open_lens(n_z=8192, fc_patch=910, fc_overlap=248,
+                                                       n_screens=2, ray_stride=1),
+                                    F).propagate()
     np.savez(out, **res)
 ''')
 
