@@ -311,7 +311,8 @@ def device_peaks(dev_index, sm_max_mhz):
             "mufu_src": src.format(f"{MUFU_PER_SM_CLK} MUFU ops/clk (nominal)")}
 
 
-KERNEL_SOURCES = ("swkb_device.cuh", "swkb_kernels.cu", "swkb_internal.h")
+KERNEL_SOURCES = ("swkb_device.cuh", "swkb_kernels.cu", "swkb_internal.h", "swkb_fc.cu",
+                  "swkb_fc_tables.h")
 
 
 def kernel_source_digest():
@@ -659,7 +660,9 @@ def patchwise_measurement(swkb, dev, pk):
         ach = work / per / 1e12
         roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": pk["fp32_tflops"],
                 "unit": "TFLOP/s", "frac": ach / pk["fp32_tflops"], "launch_ms": per * 1e3,
-                "work_per_launch": work, "work_unit": note, "peak_source": pk["fp32_src"]}
+                "work_per_launch": work, "work_unit": note, "peak_source": pk["fp32_src"],
+                "traffic": kernel_traffic({"march": "fc_march", "resum": "fc_resum",
+                                           "fft": "fc_modes"}[dom])}
     resum_mufu = None
     if st["kernel_timed"]["resum"]:
         per = st["kernel_ms"]["resum"] / 1e3 / st["kernel_timed"]["resum"]
