@@ -116,16 +116,14 @@ __global__ void __launch_bounds__(FC_MODES_THREADS) k_fc_modes(const FcModesArgs
       si += __shfl_xor_sync(0xffffffffu, si, o);
     }
     if (lane == 0) {
-      // nn s0 < 2^11 2^20: no overflow
-      const double2 rot = p.tw[mod_np(nn * (unsigned)s0, Np, p.np_magic)];
+      // (sr + i si) rot exp(i phi) / N_p in the plan's type; nn s0 < 2^11 2^20
+      const V rot = tw[mod_np(nn * (unsigned)s0, Np, p.np_magic)];
       const V ep = p.ephi[i];
-      const double er = (double)ep.x, ei = (double)ep.y;
-      // (sr + i si) rot exp(i phi) / N_p
-      const double xr = (double)sr * rot.x - (double)si * rot.y;
-      const double xi = (double)sr * rot.y + (double)si * rot.x;
+      const T xr = sr * rot.x - si * rot.y, xi = sr * rot.y + si * rot.x;
+      const T inv = (T)p.inv_Np;
       V c;
-      c.x = (T)((xr * er - xi * ei) * p.inv_Np);
-      c.y = (T)((xr * ei + xi * er) * p.inv_Np);
+      c.x = (xr * ep.x - xi * ep.y) * inv;
+      c.y = (xr * ep.y + xi * ep.x) * inv;
       p.cf[(long long)pt * p.M + i] = c;
     }
   }
