@@ -22,16 +22,17 @@ C_SOURCE = r"""
 #include <stdlib.h>
 #include "swkb.h"
 
-/* problem file: int32 n_p, n_z, bc, precision, ray_stride, rk4_steps, n_screens;
+/* problem file: int32 n_p, n_z, bc, precision, ray_stride, rk4_steps, n_screens,
+   fc_patch, fc_overlap;
    double z0_p, dz_p, k, z_a, z_b, dx, theta_max;
    double eps[n_p], eps_z[n_p], eps_zz[n_p]; double u0[2 n_z] */
 int main(int argc, char** argv) {
   if (argc != 3) return 2;
   FILE* f = fopen(argv[1], "rb");
   if (!f) return 3;
-  int32_t hdr[7];
+  int32_t hdr[9];
   double d[7];
-  if (fread(hdr, sizeof(int32_t), 7, f) != 7 || fread(d, sizeof(double), 7, f) != 7) return 4;
+  if (fread(hdr, sizeof(int32_t), 9, f) != 9 || fread(d, sizeof(double), 7, f) != 7) return 4;
   const int n_p = hdr[0], n_z = hdr[1];
   double* tab = malloc(sizeof(double) * 3 * (size_t)n_p);
   double* u0 = malloc(sizeof(double) * 2 * (size_t)n_z);
@@ -48,6 +49,8 @@ int main(int argc, char** argv) {
   opt.ray_stride = hdr[4];
   opt.rk4_steps = hdr[5];
   opt.theta_max = d[6];
+  opt.fc_patch = hdr[7];
+  opt.fc_overlap = hdr[8];
   swkb_plan* plan = NULL;
   swkb_status st = swkb_plan_create(&prof, d[2], &dom, n_z, d[5], &opt, &plan);
   if (st != SWKB_OK) { fprintf(stderr, "create: %s\n", swkb_last_error()); return 10 + st; }
@@ -66,15 +69,23 @@ int main(int argc, char** argv) {
 """
 
 
+PROBLEMS = {
+    "grounded-duct": lambda: w.config_surface_duct_small(n_screens=3).with_(absorber_frac=0.0),
+    "open-lens": lambda: w.config_open_lens(n_z=1000, fc_patch=280, fc_overlap=100,
+                                            n_screens=2),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PROBLEMS))
 @pytest.mark.parametrize("prec", [swkb.SWKB_FP64, swkb.SWKB_MIXED])
-def test_c_program_matches_the_binding(tmp_path, prec):
+def test_c_program_matches_the_binding(tmp_path, prec, name):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
-    pb = w.config_surface_duct_small(n_screens=3).with_(absorber_frac=0.0)
+    pb = PROBLEMS[name]()
     pr = pb.profile
     src = tmp_path / "client.c"
     src.write_text(C_SOURCE)
@@ -85,8 +96,8 @@ def test_c_program_matches_the_binding(tmp_path, prec):
                    capture_output=True)
     blob = tmp_path / "problem.bin"
     with open(blob, "wb") as f:
-        np.array([pr.n_p, pb.n_z, pb.bc, prec, pb.ray_stride, pb.rk4_steps, pb.n_screens],
-                 np.int32).tofile(f)
+        np.array([pr.n_p, pb.n_z, pb.bc, prec, pb.ray_stride, pb.rk4_steps, pb.n_screens,
+                  pb.fc_patch, pb.fc_overlap], np.int32).tofile(f)
         np.array([pr.z0, pr.dz, pb.k, pb.z_a, pb.z_b, pb.dx, pb.theta_max], np.float64).tofile(f)
         np.concatenate([pr.eps[0], pr.eps_z[0], pr.eps_zz[0]]).astype(np.float64).tofile(f)
         np.ascontiguousarray(pb.u0, np.complex128).view(np.float64).tofile(f)
