@@ -70,7 +70,7 @@ import math
 
 import numpy as np
 
-from .swkb_oracle import PERIODIC, Oracle, RangeError
+from .swkb_oracle import PERIODIC, CausticError, Oracle, RangeError
 
 OPEN = 3
 
@@ -245,6 +245,64 @@ class FCOracle:
                 r_m, a_m = self.base.interpolate(delta[i], (rays["r"][i], S * rays["a"][i]))
                 base = 2.0 * math.pi * ((int(n) * (m - sp)) % self.Np) / self.Np
                 out += c[p, i] * a_m * np.exp(1j * (base + pb.k * r_m))
+        return out
+
+    def screen_points(self, u: np.ndarray, q: int, ms) -> np.ndarray:
+        """screen() at the grid points ms only, for fields too large for the
+        whole screen: the same patch modes, and for each point only the rays
+        launched near it (a window of the launch grid that the steepest kept
+        mode cannot cross in one screen, widened until every mode's stencil
+        around the point lies inside it); per patch and mode the same bracket,
+        Lagrange weights and term as screen(), added in the same order."""
+        pb = self.pb
+        u = np.asarray(u, dtype=np.complex128)
+        c = self.patch_modes(u)
+        s_all = self.launch_points()
+        lam = 2.0 * math.pi / pb.k
+        kmax = self.n_max * lam / self.Lp
+        reach = pb.dx * kmax / math.sqrt(1.0 - kmax * kmax)
+        out = np.zeros(len(ms), dtype=np.complex128)
+        for idx, m in enumerate(ms):
+            half = int(math.ceil((reach + 4 * self.R * self.h) / (self.R * self.h))) + 4
+            while True:
+                jc = int(np.searchsorted(s_all, pb.z_a + self.h * m))
+                j0 = max(jc - half, 0)
+                j1 = min(jc + half, self.NRT - 1)
+                s = s_all[j0:j1 + 1]
+                rays = self.base.march(q, self.kappa[:, None], s[None, :])
+                delta = (rays["z"] - pb.z_a) / self.h
+                if np.any(np.diff(delta, axis=1) <= 0):
+                    raise CausticError("ray landings not increasing (rays crossed)")
+                jj = np.array([np.searchsorted(row, m, side="right") - 1 for row in delta])
+                if jj.min() >= 1 and jj.max() <= delta.shape[1] - 3:
+                    break
+                if j0 == 0 and j1 == self.NRT - 1:
+                    raise RangeError("ghost rays do not cover the screen")
+                half *= 2
+            u_launch = (s - pb.z_a) / self.h
+            acc = 0j
+            for p in range(self.patches.P):
+                S = self.patches.weight(p, u_launch)
+                if not np.any(S):
+                    continue            # every term of this patch is exactly zero here
+                sp = int(self.patches.start[p])
+                for i, n in enumerate(self.n):
+                    j = jj[i]
+                    x = [delta[i, j + o] for o in (-1, 0, 1, 2)]
+                    vals = []
+                    for v in (rays["r"][i], S * rays["a"][i]):
+                        f = [v[j + o] for o in (-1, 0, 1, 2)]
+                        tot = 0.0
+                        for a in range(4):
+                            wgt = 1.0
+                            for b in range(4):
+                                if b != a:
+                                    wgt *= (m - x[b]) / (x[a] - x[b])
+                            tot += wgt * f[a]
+                        vals.append(tot)
+                    base = 2.0 * math.pi * ((int(n) * (m - sp)) % self.Np) / self.Np
+                    acc += c[p, i] * vals[1] * np.exp(1j * (base + pb.k * vals[0]))
+            out[idx] = acc
         return out
 
     def propagate(self, u0: np.ndarray, q0: int = 0, n_screens: int | None = None,

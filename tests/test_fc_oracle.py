@@ -255,3 +255,14 @@ def test_library_continuation_table_matches_the_oracle(tables):
     want = A @ Q.T
     assert lib.shape == (want.size,)
     assert np.max(np.abs(lib.reshape(want.shape) - want)) <= 1e-15 * np.max(np.abs(want))
+
+
+def test_screen_points_equal_the_whole_screen(tables):
+    """The sampled form used at full size gives the whole screen's values:
+    the same rays, brackets, weights and terms, summed in the same order."""
+    pb = P.open_problem(144, 48, 3, 52.0, 6.0, 5.0, n_screens=1)
+    o = F.FCOracle(pb)
+    whole = o.screen(pb.u0, 0)
+    ms = [0, 1, 47, 96, 120, 143, 190, 240, pb.n_z - 2, pb.n_z - 1]
+    got = o.screen_points(pb.u0, 0, ms)
+    assert np.max(np.abs(got - whole[ms])) <= 1e-13 * np.max(np.abs(whole))

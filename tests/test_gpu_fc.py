@@ -135,3 +135,25 @@ def test_absorber_and_planes_are_refused():
         swkb.Plan(pb.with_(absorber_frac=0.1))
     with pytest.raises(swkb.SwkbError):
         swkb.Plan(pb, planes=2)
+
+
+@pytest.mark.parametrize("prec,tol", [(swkb.SWKB_FP64, FP64_TOL), (swkb.SWKB_MIXED, MIXED_TOL)])
+def test_open_lens_full_size_sampled_against_oracle(prec, tol):
+    """The bench's patch-wise workload at full size (N_z = 131072, 188
+    patches, R = 8, the launch shapes bench.py uses): screens 0 and 1 on the
+    GPU, sampled points of each against the oracle's screen_points, the
+    second screen started from the GPU's own first-screen field."""
+    pb = w.config_open_lens()
+    plan = swkb.Plan(pb, prec)
+    f1 = plan.propagate(n_screens=1)
+    f2 = plan.propagate(u0=f1, q0=1, n_screens=1)
+    o = FCOracle(pb)
+    rng = np.random.default_rng(17)
+    strong = np.flatnonzero(np.abs(f1) > 0.05 * np.abs(f1).max())
+    overlap = np.array([int(o.patches.start[p]) + pb.fc_overlap // 2
+                        for p in range(1, o.patches.P)])
+    overlap = overlap[np.abs(f1[overlap]) > 1e-3 * np.abs(f1).max()]
+    ms = np.unique(np.concatenate([rng.choice(strong, 10, replace=False), overlap[:4]]))
+    for q, u_in, got in ((0, pb.u0, f1), (1, f1, f2)):
+        want = o.screen_points(u_in, q, ms)
+        assert np.max(np.abs(got[ms] - want)) <= tol * np.max(np.abs(got))
