@@ -184,7 +184,9 @@ __global__ void __launch_bounds__(FC_WARPS * 32) k_fc_resum(const FcResumArgs<T>
   // ray j of mode i: landing offset, phase and the complex amplitude
   // a_j (S^{p0}(z_j) cf[p0][i] + S^{p0+1}(z_j) cf[p0+1][i])
   auto fetch = [&](int i, int j, T& d, T& ph, T& ar, T& ai) {
-    const long long o = bchk((long long)j * p.M + i, nrays, st);
+    // NRT M < 2^32 (at most 2^20 + 2 G rays of 2047 modes)
+    const unsigned o = (unsigned)bchk((long long)((unsigned)j * (unsigned)p.M + (unsigned)i),
+                                      nrays, st);
     d = ld<LD_NC>(p.d + o);
     ph = ld<LD_NC>(p.ph + o);
     const T a = ld<LD_NC>(p.a + o);
@@ -297,26 +299,53 @@ __global__ void __launch_bounds__(FC_WARPS * 32) k_fc_resum(const FcResumArgs<T>
     Row<T> r = load_row<T>(s_cf + FC_CF * w);
     const int n = i - p.n_max;   // |n| < Np / 2
     const unsigned nn = (unsigned)(n < 0 ? n + p.Np : n);
-    // nn (m0 + x0) < 2^11 2^20: no overflow
-    unsigned nm = mod_np(nn * (unsigned)(m0 + x0), Np, p.np_magic);
+    if constexpr (sizeof(T) == 4) {
+      // the exact integer phase n m / Np mod 1 of the run's middle point,
+      // moved into [-1/2, 1/2), and n / Np (|n / Np| < 1/2) per point from it:
+      // the argument of the sine stays within about two turns
+      const unsigned nmc = mod_np(nn * (unsigned)(m0 + x0 + PW / 2), Np, p.np_magic);
+      T bc = T(nmc) * invNp;
+      bc = bc >= T(0.5) ? bc - T(1) : bc;
+      const T nNp = T(n) * invNp;
 #pragma unroll
-    for (int q = 0; q < PW; ++q) {
-      const T xv = xv0 + T(q);
-      while (w < W - 3 && r.X2 <= xv) {
-        ++w;
-        r = load_row<T>(s_cf + FC_CF * w);
+      for (int q = 0; q < PW; ++q) {
+        const T xv = xv0 + T(q);
+        while (w < W - 3 && r.X2 <= xv) {
+          ++w;
+          r = load_row<T>(s_cf + FC_CF * w);
+        }
+        const T tau = xv - r.X1;
+        const T phv = ((r.b3 * tau + r.b2) * tau + r.b1) * tau + r.b0;
+        const T ar = ((r.r3 * tau + r.r2) * tau + r.r1) * tau + r.r0;
+        const T ai = ((r.i3 * tau + r.i2) * tau + r.i1) * tau + r.i0;
+        const T t = fmaf(T(q - PW / 2), nNp, bc) + phv;
+        T sn, cs;
+        sincos_turns(t, &sn, &cs);
+        accr[q] += ar * cs - ai * sn;
+        acci[q] += ar * sn + ai * cs;
       }
-      const T tau = xv - r.X1;
-      const T phv = ((r.b3 * tau + r.b2) * tau + r.b1) * tau + r.b0;
-      const T ar = ((r.r3 * tau + r.r2) * tau + r.r1) * tau + r.r0;
-      const T ai = ((r.i3 * tau + r.i2) * tau + r.i1) * tau + r.i0;
-      const T t = minus_rint(T(nm) * invNp + phv);
-      T sn, cs;
-      sincos_turns(t, &sn, &cs);
-      accr[q] += ar * cs - ai * sn;
-      acci[q] += ar * sn + ai * cs;
-      nm += nn;
-      if (nm >= Np) nm -= Np;
+    } else {
+      // nn (m0 + x0) < 2^11 2^20: no overflow
+      unsigned nm = mod_np(nn * (unsigned)(m0 + x0), Np, p.np_magic);
+#pragma unroll
+      for (int q = 0; q < PW; ++q) {
+        const T xv = xv0 + T(q);
+        while (w < W - 3 && r.X2 <= xv) {
+          ++w;
+          r = load_row<T>(s_cf + FC_CF * w);
+        }
+        const T tau = xv - r.X1;
+        const T phv = ((r.b3 * tau + r.b2) * tau + r.b1) * tau + r.b0;
+        const T ar = ((r.r3 * tau + r.r2) * tau + r.r1) * tau + r.r0;
+        const T ai = ((r.i3 * tau + r.i2) * tau + r.i1) * tau + r.i0;
+        const T t = minus_rint(T(nm) * invNp + phv);
+        T sn, cs;
+        sincos_turns(t, &sn, &cs);
+        accr[q] += ar * cs - ai * sn;
+        acci[q] += ar * sn + ai * cs;
+        nm += nn;
+        if (nm >= Np) nm -= Np;
+      }
     }
   }
   __syncthreads();
