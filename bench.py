@@ -311,26 +311,28 @@ def device_peaks(dev_index, sm_max_mhz):
             "mufu_src": src.format(f"{MUFU_PER_SM_CLK} MUFU ops/clk (nominal)")}
 
 
-KERNEL_SOURCES = ("swkb_device.cuh", "swkb_kernels.cu", "swkb_internal.h", "swkb_fc.cu",
-                  "swkb_fc_tables.h")
+KERNEL_SOURCES = ("swkb_device.cuh", "swkb_kernels.cu", "swkb_internal.h")
+FC_KERNEL_SOURCES = ("swkb_device.cuh", "swkb_internal.h", "swkb_fc.cu", "swkb_fc_tables.h")
 
 
-def kernel_source_digest():
+def kernel_source_digest(sources=KERNEL_SOURCES):
     """16 hex digits of the SHA-256 of the device-code sources, in order."""
     h = hashlib.sha256()
-    for name in KERNEL_SOURCES:
+    for name in sources:
         h.update(open(os.path.join(ROOT, "paper_2301_03814_gb300", "csrc", name), "rb").read())
     return h.hexdigest()[:16]
 
 
 def kernel_traffic(kind):
     """DRAM bytes per launch from the committed ncu summary, when it was taken
-    on the current kernel source (else None)."""
+    on the current kernel sources (the periodic kernels', or for kinds fc_*
+    the patch-wise kernels'; else None)."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         rec = json.load(open(path))
-        digest = kernel_source_digest()
-        if rec.get("kernels_sha256_16") != digest:
+        fc = kind.startswith("fc_")
+        digest = kernel_source_digest(FC_KERNEL_SOURCES if fc else KERNEL_SOURCES)
+        if rec.get("fc_kernels_sha256_16" if fc else "kernels_sha256_16") != digest:
             return None
         return rec.get("bytes_per_launch", {}).get(kind)
     except (OSError, ValueError):
