@@ -398,17 +398,30 @@ size_t fc_modes_smem_bytes(int Np) {
 
 template <typename T>
 cudaError_t prepare_fc_kernels(int resum_smem, int modes_smem) {
-  cudaError_t e = cudaFuncSetAttribute(k_fc_modes<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       modes_smem);
+  // The limit is a per-device property of the kernel shared by every plan in
+  // the process: raise it to the device's opt-in maximum (never lower it, or a
+  // plan with a shorter period or smaller tiles would break another plan's
+  // launches).
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_fc_resum<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           resum_smem);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_fc_resum<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           resum_smem);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_fc_resum<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              resum_smem);
+  if (resum_smem > optin || modes_smem + (int)(2 * FC_D * sizeof(double2)) > optin)
+    return cudaErrorInvalidValue;
+  const void* fs[] = {(const void*)k_fc_modes<T>, (const void*)k_fc_resum<T, 2>,
+                      (const void*)k_fc_resum<T, 4>, (const void*)k_fc_resum<T, 8>};
+  for (const void* f : fs) {
+    // the dynamic limit plus the kernel's static shared memory must stay
+    // within the opt-in maximum
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, f);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 template <typename T>

@@ -157,3 +157,16 @@ def test_open_lens_full_size_sampled_against_oracle(prec, tol):
     for q, u_in, got in ((0, pb.u0, f1), (1, f1, f2)):
         want = o.screen_points(u_in, q, ms)
         assert np.max(np.abs(got[ms] - want)) <= tol * np.max(np.abs(got))
+
+
+def test_plans_of_different_sizes_coexist():
+    """The kernels' shared-memory limit is process-wide: creating a plan with
+    a shorter continued period and smaller tiles after a larger one must not
+    break the larger plan's launches (both FP64: the largest staging)."""
+    big = lens(ray_stride=1, P_=2, n_pat=1600, n_ov=200, zc=300.0, n_screens=1)
+    small = lens(n_screens=1)
+    p_big = swkb.Plan(big, precision=swkb.SWKB_FP64)
+    first = p_big.propagate()
+    p_small = swkb.Plan(small, precision=swkb.SWKB_FP64)
+    p_small.propagate()
+    assert np.array_equal(p_big.propagate(), first)
