@@ -25,13 +25,18 @@ def _need_gpu():
 
 def mix():
     """Uneven requests: periodic unit-wavelength runs of different lengths, a
-    grounded duct in both precisions, a homogeneous Dirichlet case."""
+    grounded duct in both precisions, a homogeneous Dirichlet case, and open
+    intervals through the patch-wise continuation in both precisions."""
     return [
         (w.config_unit_periodic(n_screens=10), swkb.SWKB_FP64),
         (w.config_surface_duct_small(n_screens=6), swkb.SWKB_MIXED),
+        (w.config_open_lens(n_z=1000, fc_patch=280, fc_overlap=100, n_screens=3),
+         swkb.SWKB_MIXED),
         (w.config_unit_periodic(n_screens=3), swkb.SWKB_MIXED),
         (w.config_surface_duct_small(n_screens=4), swkb.SWKB_FP64),
         (w.config_homogeneous(bc=w.BC_DIRICHLET, ray_stride=2), swkb.SWKB_MIXED),
+        (w.config_open_lens(n_z=1000, fc_patch=280, fc_overlap=100, n_screens=2),
+         swkb.SWKB_FP64),
         (w.config_unit_periodic(n_screens=7), swkb.SWKB_FP64),
     ]
 
