@@ -179,8 +179,10 @@ typedef struct {
                              itself; always 0 for FP64 plans)                 */
   int32_t ctas_per_sm;    /* resummation CTAs per SM the mode groups target  */
   int32_t fc_patches;     /* SWKB_BC_OPEN: patches (else 0); n_fft is then n_z
-                             rounded up to 256 (the points the rays cover and
-                             the sum runs over) and period the patches' N_p dz */
+                             rounded up to a multiple of 64 (the points the
+                             rays cover and the sum runs over; the permittivity
+                             table must cover their reach) and period the
+                             patches' N_p dz */
   int32_t fc_period_points; /* SWKB_BC_OPEN: N_p = fc_patch + 25 (else 0)     */
 } swkb_plan_info;
 

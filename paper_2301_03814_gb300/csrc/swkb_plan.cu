@@ -1371,7 +1371,7 @@ bool valid_tiling(const swkb_plan* p, const Tiling& t) {
 Tiling default_tiling(const swkb_plan* p) {
   Tiling t;
   t.PW = p->R >= 8 ? 8 : (p->R >= 2 ? 4 : 2);
-  while (32 * t.PW > (p->sym ? p->N / 2 : p->N)) t.PW /= 2;
+  while (32 * t.PW > (p->sym ? p->N / 2 : p->N) || (p->fc && p->N % (32 * t.PW))) t.PW /= 2;
   t.ctas_per_sm = 6;
   // N1 ~ sqrt(M): pass 1 costs N N1, pass 2 M N2
   t.N1 = 1;
@@ -1437,8 +1437,9 @@ swkb_status configure(swkb_plan* p, const swkb_profile* prof, double k, const sw
   const double H = dom->z_b - dom->z_a;
   p->fc = dom->bc == SWKB_BC_OPEN;
   if (p->fc) {
-    // patch-wise continuation: the rays and the sum cover n_z rounded up to
-    // whole resummation tiles; the extra points belong to no patch
+    // patch-wise continuation: the rays and the sum cover n_z rounded up to a
+    // multiple of 64 (whole resummation tiles of 64, 128 or 256 points that
+    // divide it); the extra points belong to no patch
     p->fc_pat = opt.fc_patch;
     p->fc_ov = opt.fc_overlap;
     p->fc_stride = p->fc_pat - p->fc_ov;
@@ -1457,7 +1458,7 @@ swkb_status configure(swkb_plan* p, const swkb_profile* prof, double k, const sw
     p->fc_P = (n_z - p->fc_pat) / p->fc_stride + 1;
     if (opt.absorber_frac != 0.0 || opt.planes > 1)
       return fail(SWKB_ERR_INVALID_ARG, "patch-wise plans take no absorber and no inner planes");
-    p->N = (n_z + 255) / 256 * 256;
+    p->N = (n_z + 63) / 64 * 64;
     p->L = p->fc_Np * (H / n_z);
   } else {
     p->N = p->mirror ? 2 * n_z : n_z;

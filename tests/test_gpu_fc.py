@@ -55,6 +55,11 @@ CASES = {
     "lens-1-patch": lambda: lens(P_=1, n_pat=240, n_ov=48, zc=40.0, n_screens=3),
     "lens-range-dependent": lambda: lens(cols=2, n_screens=3),
     "homogeneous-6x120": lambda: P.open_problem(120, 40, 6, 90.0, -7.0, 5.0, n_screens=2),
+    # the smallest accepted patch (16 points, 8 shared) and the longest
+    # continued period (N_p = 2048, one patch)
+    "edge-min-patch": lambda: P.open_problem(16, 8, 7, 32 * P.STEP, 0.0, 1.0, n_screens=1),
+    "edge-max-period": lambda: P.open_problem(2023, 500, 1, 1011 * P.STEP, 5.0, 3.0,
+                                              n_screens=1),
 }
 
 _oracle = {}
@@ -89,7 +94,7 @@ def test_modes_and_rays_match_the_oracle_mode_set():
     o = FCOracle(pb)
     info = swkb.Plan(pb).info
     assert info.n_max == o.n_max and info.n_ghost == o.G
-    assert info.n_fft == (pb.n_z + 255) // 256 * 256
+    assert info.n_fft == (pb.n_z + 63) // 64 * 64
     assert info.n_rays_total == info.n_fft // pb.ray_stride + 2 * o.G
     assert abs(info.period - o.Lp) < 1e-12 * o.Lp
 
