@@ -147,6 +147,24 @@ def cpu_baseline(pb):
                       f"(one per host core), bit-identical to the serial oracle"}
 
 
+def patchwise_cpu_baseline():
+    """The continuation oracle (serial numpy FP64, one core) on a bounded
+    sample of the patch-wise workload: one whole screen of the open lens at
+    N_z = 8192 (12 patches, 539 modes per patch)."""
+    from oracle.fc_oracle import FCOracle, fc_gram_tables
+    from paper_2301_03814_gb300 import workloads as w
+    pb = w.config_open_lens(n_z=8192, fc_patch=910, fc_overlap=248, n_screens=1)
+    fc_gram_tables()                       # the tables once, outside the timing
+    o = FCOracle(pb)
+    t = time.perf_counter()
+    o.screen(pb.u0, 0)
+    dt = time.perf_counter() - t
+    model, _ = host_cpu()
+    return {"value": pb.n_z / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu": model,
+            "sample": "1 whole screen of the open lens at N_z = 8192 (12 patches of 910 "
+                      "points, 539 modes per patch, R = 8), serial numpy FP64 oracle"}
+
+
 def run_reference(args, rank, world):
     pb = workload()
     if rank != 0:
@@ -983,6 +1001,8 @@ def run_ours(args, world, rank, local):
         line["paper_scale"] = paper_scale_measurement(swkb, dev)
     if world == 1 and not args.no_patchwise:
         line["patchwise"] = patchwise_measurement(swkb, dev, pk)
+        if not args.no_cpu_baseline:
+            line["patchwise"]["cpu_baseline"] = patchwise_cpu_baseline()
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(pb)
     print(json.dumps(line), flush=True)
