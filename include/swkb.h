@@ -152,8 +152,9 @@ typedef struct {
      floor(sin(theta_max) N_p dz / lambda) or n_max); the partition of unity
      S^p rises and falls over fc_overlap points (a C-infinity step), also at
      the interval's two ends; every ray of mode n launched at z_j carries
-     sum_p S^p(z_j) w_n^p / N_p.  No absorber, no inner planes, no autotune;
-     swkb_debug_screen and the batch kernel refuse these plans. */
+     sum_p S^p(z_j) w_n^p / N_p.  No absorber and no autotune; inner planes
+     (swkb_propagate_planes) as for the other plans; swkb_debug_screen and the
+     batch kernel refuse these plans. */
   int32_t fc_patch;
   int32_t fc_overlap;
 } swkb_options;

@@ -229,11 +229,38 @@ class FCOracle:
 
     def screen(self, u: np.ndarray, q: int) -> np.ndarray:
         """Gamma_q -> Gamma_{q+1} on the n_z grid points (F1-F6)."""
-        pb = self.pb
         u = np.asarray(u, dtype=np.complex128)
-        c = self.patch_modes(u)
+        return self.ray_sum(self.patch_modes(u), q, None)
+
+    def screen_planes(self, u: np.ndarray, q: int, planes: int):
+        """Fields of screen q on the planes x_q + j dx / planes, j = 1..planes
+        (the periodic oracle's R15 applied to the patches): the screen's
+        patch modes, their rays marched j rk4_steps / planes steps, summed as
+        on the screen.  The last plane is the screen's own field."""
+        pb = self.pb
+        if planes < 1 or pb.rk4_steps % planes:
+            raise ValueError("planes must divide rk4_steps")
+        c = self.patch_modes(np.asarray(u, dtype=np.complex128))
+        return [self.ray_sum(c, q, j * pb.rk4_steps // planes) for j in range(1, planes + 1)]
+
+    def propagate_planes(self, u0: np.ndarray, q0: int, n_screens: int, planes: int):
+        """Fields on every plane of screens q0 .. q0+n_screens-1, rows ordered
+        (screen, plane); each screen starts from the previous screen's last
+        plane."""
+        u = np.asarray(u0, dtype=np.complex128)
+        rows = []
+        for q in range(q0, q0 + n_screens):
+            fields = self.screen_planes(u, q, planes)
+            rows.extend(fields)
+            u = fields[-1]
+        return np.array(rows)
+
+    def ray_sum(self, c: np.ndarray, q: int, steps) -> np.ndarray:
+        """Eq. ifft_eq_phi_patches carried to the plane reached after `steps`
+        RK4 steps of screen q (None: the next screen), F5-F6."""
+        pb = self.pb
         s = self.launch_points()
-        rays = self.base.march(q, self.kappa[:, None], s[None, :])
+        rays = self.base.march(q, self.kappa[:, None], s[None, :], steps=steps)
         delta = (rays["z"] - pb.z_a) / self.h
         u_launch = (s - pb.z_a) / self.h
         m = np.arange(pb.n_z)

@@ -424,6 +424,29 @@ cudaError_t prepare_fc_kernels(int resum_smem, int modes_smem) {
   return cudaSuccess;
 }
 
+// out[p][n] = cf[p][n] f[n]: the patches' coefficients carried to a plane
+// inside the screen (f: exp(i k (j / P - 1) dx Pbar_n)).
+template <typename T>
+__global__ void k_fc_cscale(const typename C2<T>::type* __restrict__ cf,
+                            const typename C2<T>::type* __restrict__ f,
+                            typename C2<T>::type* __restrict__ out, int PM, int M) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= PM) return;
+  const typename C2<T>::type a = cf[k], b = f[k % M];
+  typename C2<T>::type c;
+  c.x = a.x * b.x - a.y * b.y;
+  c.y = a.x * b.y + a.y * b.x;
+  out[k] = c;
+}
+
+template <typename T>
+cudaError_t launch_fc_cscale(const typename C2<T>::type* cf, const typename C2<T>::type* f,
+                             typename C2<T>::type* out, int P, int M, cudaStream_t s) {
+  const int PM = P * M;
+  k_fc_cscale<T><<<(PM + 255) / 256, 256, 0, s>>>(cf, f, out, PM, M);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_fc_modes(const FcModesArgs<T>& a, cudaStream_t s) {
   const dim3 grid(a.P, (a.M + FC_MODES_PER_CTA - 1) / FC_MODES_PER_CTA);
@@ -452,6 +475,10 @@ template cudaError_t prepare_fc_kernels<double>(int, int);
 template cudaError_t launch_fc_modes<float>(const FcModesArgs<float>&, cudaStream_t);
 template cudaError_t launch_fc_modes<double>(const FcModesArgs<double>&, cudaStream_t);
 template cudaError_t launch_fc_resum<float>(const FcResumArgs<float>&, cudaStream_t);
+template cudaError_t launch_fc_cscale<float>(const float2*, const float2*, float2*, int, int,
+                                             cudaStream_t);
+template cudaError_t launch_fc_cscale<double>(const double2*, const double2*, double2*, int, int,
+                                              cudaStream_t);
 template cudaError_t launch_fc_resum<double>(const FcResumArgs<double>&, cudaStream_t);
 
 }  // namespace swkb

@@ -170,6 +170,11 @@ struct FcResumArgs {
 
 template <typename T> cudaError_t launch_fc_modes(const FcModesArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_fc_resum(const FcResumArgs<T>& a, cudaStream_t s);
+// out[p][n] = cf[p][n] f[n] for P patches of M modes (planes inside a screen)
+template <typename T> cudaError_t launch_fc_cscale(const typename C2<T>::type* cf,
+                                                   const typename C2<T>::type* f,
+                                                   typename C2<T>::type* out, int P, int M,
+                                                   cudaStream_t s);
 template <typename T> size_t fc_resum_smem_bytes(int wcap, int tile_points);
 template <typename T> size_t fc_modes_smem_bytes(int Np);
 template <typename T> cudaError_t prepare_fc_kernels(int resum_smem, int modes_smem);

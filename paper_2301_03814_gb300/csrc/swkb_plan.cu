@@ -173,6 +173,7 @@ struct swkb_plan {
   void* fc_cont = nullptr;    // [FC_C][FC_D] continuation operator, FP64
   void* fc_tw = nullptr;      // [Np] exp(-2 pi i k / Np), FP64
   void* fc_cf = nullptr;      // [P][M] mode coefficients of every patch
+  void* fc_cf_plane = nullptr;  // [P][M] the same carried to a plane inside the screen
   int* fc_win_p = nullptr;    // [NRT] first patch weighting launch point j
   void* fc_win_s = nullptr;   // [NRT] (S^{p0}, S^{p0+1}) at launch point j
 };
@@ -449,6 +450,7 @@ swkb_status build_fc(swkb_plan* p) {
     TRY(upload<T>(p, &p->fc_win_s, ws));
   }
   TRY(dev_alloc(p, &p->fc_cf, (size_t)p->fc_P * p->M * sizeof(V)));
+  if (p->planes > 1) TRY(dev_alloc(p, &p->fc_cf_plane, (size_t)p->fc_P * p->M * sizeof(V)));
   return SWKB_OK;
 }
 
@@ -788,11 +790,11 @@ FcModesArgs<T> fc_modes_args(const swkb_plan* p) {
 
 template <typename T>
 FcResumArgs<T> fc_resum_args(const swkb_plan* p, const T* d, const T* ph, const T* a,
-                             const int* jlo) {
+                             const int* jlo, const void* cf = nullptr) {
   using V = typename C2<T>::type;
   FcResumArgs<T> r;
   r.d = d; r.ph = ph; r.a = a; r.jlo = jlo;
-  r.cf = (const V*)p->fc_cf;
+  r.cf = (const V*)(cf ? cf : p->fc_cf);
   r.win_p = p->fc_win_p;
   r.win_s = (const V*)p->fc_win_s;
   r.M = p->M; r.NRT = p->NRT; r.G = p->G; r.R = p->R; r.N = p->N; r.TM = p->TM;
@@ -1056,9 +1058,75 @@ swkb_status enqueue_overlapped(swkb_plan* p, const double* u0, int q0, int n, do
 // screen's modes, its rays stopped after j N_t / P RK4 steps, the same
 // interpolation and sum with the range-phase carry of that plane, and no
 // absorber.  Uses the inner-plane buffers (P <= the plan's planes option).
+// enqueue_planes() for a patch-wise plan: the patches' modes once per
+// screen, carried to each inner plane by exp(i k (j/P - 1) dx Pbar_n).
+template <typename T>
+swkb_status enqueue_planes_fc(swkb_plan* p, const double* u0, int q0, int n, int P,
+                              double* out_dev, double* out_host) {
+  using V = typename C2<T>::type;
+  cudaStream_t s = p->stream;
+  p->rays_ready = false;
+  const size_t nb = 2 * sizeof(double) * p->n_z;
+  const size_t rays = (size_t)p->NRT * p->Mr;
+  TRY(timed(p, SWKB_KERNEL_INIT, 1,
+            [&] { return launch_init<T>(u0, p->n_z, p->n_z, 0, (V*)p->u, s); }));
+  int row = 0;
+  auto emit = [&]() -> swkb_status {
+    const int idx = row++;
+    double* dst = out_dev ? out_dev + 2 * (size_t)idx * p->n_z : p->io;
+    TRY(timed(p, SWKB_KERNEL_OUTPUT, 1,
+              [&] { return launch_output<T>((const V*)p->u, 0, p->n_z, dst, s); }));
+    if (!out_dev)
+      CK(cudaMemcpyAsync(out_host + 2 * (size_t)idx * p->n_z, p->io, nb, cudaMemcpyDeviceToHost,
+                         s));
+    return SWKB_OK;
+  };
+  auto reduce = [&]() -> swkb_status {
+    ReduceArgs<T> r{(const V*)p->part, p->n_groups, p->N, nullptr, 0, 0, (V*)p->u};
+    TRY(timed(p, SWKB_KERNEL_REDUCE, 1, [&] { return launch_reduce<T>(r, s); }));
+    return SWKB_OK;
+  };
+  for (int q = q0; q < q0 + n; ++q) {
+    const FcModesArgs<T> f = fc_modes_args<T>(p);
+    TRY(timed(p, SWKB_KERNEL_FFT, 1, [&] { return launch_fc_modes<T>(f, s); }));
+    MarchArgs<T> ma = march_args<T>(p, q);
+    if (P > 1) {
+      ma.plane_steps = p->Nt / P;
+      ma.pl_d = (T*)p->pl_d; ma.pl_ph = (T*)p->pl_ph; ma.pl_a = (T*)p->pl_a;
+    }
+    const bool multi = p->n_cols > 1;
+    TRY(timed(p, SWKB_KERNEL_MARCH, 1, [&] { return launch_march<T>(ma, multi, s); }));
+    for (int j = 1; j < P; ++j) {
+      const size_t o = (size_t)(j - 1) * rays;
+      const BracketArgs<T> b = bracket_args<T>(p, (const T*)p->pl_d + o);
+      TRY(timed(p, SWKB_KERNEL_BRACKET, 1, [&] { return launch_bracket<T>(b, s); }));
+      const V* fj = (const V*)p->ephi_pl + (size_t)(j - 1) * p->M;
+      TRY(timed(p, SWKB_KERNEL_REDUCE, 1, [&] {
+        return launch_fc_cscale<T>((const V*)p->fc_cf, fj, (V*)p->fc_cf_plane, p->fc_P, p->M, s);
+      }));
+      const FcResumArgs<T> ra = fc_resum_args<T>(p, (const T*)p->pl_d + o,
+                                                 (const T*)p->pl_ph + o, (const T*)p->pl_a + o,
+                                                 p->jlo, p->fc_cf_plane);
+      TRY(timed(p, SWKB_KERNEL_RESUM, 1, [&] { return launch_fc_resum<T>(ra, s); }));
+      TRY(reduce());
+      TRY(emit());
+    }
+    const BracketArgs<T> b = bracket_args<T>(p, (const T*)p->rd);
+    TRY(timed(p, SWKB_KERNEL_BRACKET, 1, [&] { return launch_bracket<T>(b, s); }));
+    const FcResumArgs<T> ra = fc_resum_args<T>(p, (const T*)p->rd, (const T*)p->rph,
+                                               (const T*)p->ra, p->jlo);
+    TRY(timed(p, SWKB_KERNEL_RESUM, 1, [&] { return launch_fc_resum<T>(ra, s); }));
+    TRY(reduce());
+    TRY(emit());
+    p->stats.screens += 1;
+  }
+  return SWKB_OK;
+}
+
 template <typename T>
 swkb_status enqueue_planes(swkb_plan* p, const double* u0, int q0, int n, int P,
                            double* out_dev, double* out_host) {
+  if (p->fc) return enqueue_planes_fc<T>(p, u0, q0, n, P, out_dev, out_host);
   using V = typename C2<T>::type;
   cudaStream_t s = p->stream;
   p->rays_ready = false;
@@ -1456,8 +1524,8 @@ swkb_status configure(swkb_plan* p, const swkb_profile* prof, double k, const sw
       return fail(SWKB_ERR_INVALID_ARG, "fc_patch + %d = %d exceeds 2048", FC_CONT_ROWS,
                   p->fc_Np);
     p->fc_P = (n_z - p->fc_pat) / p->fc_stride + 1;
-    if (opt.absorber_frac != 0.0 || opt.planes > 1)
-      return fail(SWKB_ERR_INVALID_ARG, "patch-wise plans take no absorber and no inner planes");
+    if (opt.absorber_frac != 0.0)
+      return fail(SWKB_ERR_INVALID_ARG, "patch-wise plans take no absorber");
     p->N = (n_z + 63) / 64 * 64;
     p->L = p->fc_Np * (H / n_z);
   } else {
@@ -1611,7 +1679,7 @@ size_t device_bytes(const swkb_plan* p) {
     b -= (size_t)p->N * V * 2;                                       // no twiddles, no Y
     b += (size_t)FC_CONT_ROWS * FC_CONT_COLS * 8 + (size_t)p->fc_Np * 16   // operator, twiddles
          + (size_t)p->NRT * (sizeof(int) + V)                        // launch-point weights
-         + (size_t)p->fc_P * p->M * V;                               // patch coefficients
+         + (size_t)p->fc_P * p->M * V * (p->planes > 1 ? 2 : 1);     // patch coefficients
   }
   return b;
 }
@@ -1959,7 +2027,6 @@ swkb_status swkb_propagate_planes(swkb_plan* p, const double* u0, int32_t q0, in
   try {
     if (!p || !u0 || !u_out) return fail(SWKB_ERR_INVALID_ARG, "NULL argument");
     if (n_screens < 0 || q0 < 0) return fail(SWKB_ERR_INVALID_ARG, "negative screen count");
-    if (p->fc) return fail(SWKB_ERR_INVALID_ARG, "patch-wise plans have no inner planes");
     if (planes < 1 || p->Nt % planes)
       return fail(SWKB_ERR_INVALID_ARG, "planes (%d) must divide rk4_steps (%d)", planes, p->Nt);
     if (planes > std::max(1, p->planes))

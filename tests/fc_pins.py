@@ -207,3 +207,16 @@ def pin_homogeneous_closed_form(FC):
             want += term
             scale += np.abs(term)
     assert np.max(np.abs(got - want)) < 2e-6 * np.max(scale)
+
+
+def pin_planes_homogeneous(FC):
+    """Fields between screens (planes x_q + j dx / 4): in eps = 1 each plane
+    is the angular spectrum over j dx / 4 (same bound as the screen's pin),
+    and the last plane is the screen itself."""
+    pb = open_problem(144, 48, 3, (144 - 24) * STEP, 8.0, 5.0)
+    o = FC(pb)
+    fields = o.screen_planes(pb.u0, 0, 4)
+    for j, f in enumerate(fields, start=1):
+        want = angular_spectrum(pb.u0, j * pb.dx / 4)
+        assert np.max(np.abs(f - want)) / np.max(np.abs(want)) < 2e-6, j
+    assert np.array_equal(fields[-1], o.screen(pb.u0, 0))

@@ -48,6 +48,10 @@ def test_homogeneous_closed_form(tables):
     P.pin_homogeneous_closed_form(F.FCOracle)
 
 
+def test_planes_between_screens(tables):
+    P.pin_planes_homogeneous(F.FCOracle)
+
+
 def test_lens_against_periodic_swkb(tables):
     P.pin_against_periodic(F.FCOracle, Oracle)
 

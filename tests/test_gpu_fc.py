@@ -134,12 +134,23 @@ def test_invalid_layouts_are_refused(kw, msg):
     assert msg in str(e.value)
 
 
-def test_absorber_and_planes_are_refused():
-    pb = lens()
+def test_absorber_is_refused():
     with pytest.raises(swkb.SwkbError):
-        swkb.Plan(pb.with_(absorber_frac=0.1))
-    with pytest.raises(swkb.SwkbError):
-        swkb.Plan(pb, planes=2)
+        swkb.Plan(lens().with_(absorber_frac=0.1))
+
+
+@pytest.mark.parametrize("prec,tol", [(swkb.SWKB_FP64, FP64_TOL), (swkb.SWKB_MIXED, MIXED_TOL)])
+def test_planes_match_oracle(prec, tol):
+    """Fields on 4 planes per screen over 2 screens (range-dependent lens:
+    the planes' stage columns differ), against the oracle's planes; the last
+    plane of each screen equals the plain propagation's screen field."""
+    pb = lens(cols=2, n_screens=2)
+    want = FCOracle(pb).propagate_planes(pb.u0, 0, 2, 4)
+    plan = swkb.Plan(pb, precision=prec, planes=4)
+    got = plan.propagate_planes(4)
+    assert got.shape == want.shape
+    assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want))
+    assert np.array_equal(got[-1], plan.propagate())
 
 
 @pytest.mark.parametrize("prec,tol", [(swkb.SWKB_FP64, FP64_TOL), (swkb.SWKB_MIXED, MIXED_TOL)])
