@@ -58,7 +58,9 @@ Readings (the section gives a sketch; where it is silent this is the choice):
       landings onto the n_z grid points exactly as in the periodic method
       (R8: bracket delta_j <= m < delta_{j+1}, 4-point Lagrange), and
       u(z_m) = sum_p sum_n (w_n^p / N_p) A exp(i (2 pi n (m - s_p) / N_p + k r)).
-      Grid points outside the ghosts' cover are an error.
+      Grid points outside the ghosts' cover are an error.  Fields between
+      screens follow the periodic reading R15: the screen's patch modes,
+      their rays stopped on the plane, the same sum.
 
 Everything is float64 except the continuation tables, which are computed in
 extended precision (mpmath) and then rounded.
